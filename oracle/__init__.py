@@ -1,0 +1,21 @@
+"""CPU oracle for the selective-encryption hot path (first level of protection, Sect. 6.3.1).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check of the build entry point and
+the CPU-baseline leg of the benchmark may import this package.  The product (the CUDA
+library and its Python binding) never calls it, and it shares no code, table or constant
+generator with the CUDA path.
+
+Plain, slow, obviously correct code, following the paper step by step:
+
+  dct.py    8x8 DCT-II per channel in float64 (Sect. 6.4.2: separable 1-D basis)
+  exact.py  exact arithmetic in Z[cos(pi/16)] used to take every rounding decision on
+            the exact real value (Sect. 6.4.3: "numbers are turned back to integer")
+  aes.py    AES-128 written from FIPS-197 (S-box generated from its definition) and the
+            CTR mode of NIST SP 800-38A (Sect. 6.12: "AES with counter mode")
+  fds.py    protect / restore: DCT -> int16 -> zigzag split -> AES-CTR on Part 1, and the
+            inverse (Sect. 6.3.1, Fig. 6; Sect. 3.2 defragmentation)
+
+Every function that is not pinned by a test against something other than itself says
+"parity unpinned" in its docstring.  None does at present.
+"""
+from . import aes, dct, exact, fds  # noqa: F401
