@@ -1,0 +1,138 @@
+/*
+ * fds.h -- C ABI of the GB300 selective-protection library.
+ *
+ * The library implements the "first level of protection" of selective encryption for RGB
+ * bitmaps (Memmi, Kapusta, Lambein, Qiu, "Data Protection: Combining Fragmentation,
+ * Encryption, and Dispersion", Sect. 6.3.1, Fig. 6):
+ *
+ *   protect: every 8x8 block of every colour channel gets a 2-D DCT-II (Sect. 6.4.2); each
+ *            coefficient is rounded to int16 (Sect. 6.4.3); the coefficients at zigzag
+ *            positions 0..k form the confidential fragment (Part 1), which is encrypted with
+ *            AES-128 in counter mode (Sect. 6.12, Sect. 6.5.2); positions k+1..63 form the
+ *            public fragment (Part 2).  k = 5 is the paper's default selection [0,0], [0,1],
+ *            [1,0], [2,0], [1,1], [0,2]; k = 0 keeps only the DC coefficient (Sect. 6.2.1).
+ *   restore: decrypt Part 1, merge it with Part 2, inverse DCT, round, clamp to [0, 255]
+ *            (defragmentation, Sect. 3.2 and Sect. 5.2 Fig. 3).
+ *
+ * Conventions that the paper leaves open, fixed here:
+ *   - DCT: orthonormal DCT-II, no level shift (the DC of an 8-bit block is at most 2040,
+ *     Sect. 6.4.3); F[u][v] with u the vertical and v the horizontal frequency.
+ *   - Rounding: half away from zero, decided on the exact real value of the coefficient
+ *     (or pixel).  Every output is therefore a pure function of the input, bit for bit.
+ *   - Zigzag: the JPEG scan (anti-diagonals u + v, alternating direction, starting
+ *     [0,0], [0,1], [1,0], [2,0], ...).
+ *   - Image: H x W x 3 uint8, row-major, channels interleaved; W and H multiples of 8.
+ *   - Public fragment: int16 [H/8][W/8][3][63 - k], zigzag positions k+1..63 in order.
+ *   - Private fragment: the little-endian int16 stream [H/8][W/8][3][k + 1] (zigzag 0..k),
+ *     AES-128-CTR encrypted as one message per image: keystream block j is
+ *     AES_K(IV + j), IV the 16-byte initial counter block read as a big-endian 128-bit
+ *     integer, addition modulo 2^128 (OpenSSL's aes-128-ctr).  The caller must never reuse
+ *     a (key, counter) pair across images.
+ *
+ * Memory: every pointer argument marked "device" is a CUDA device pointer on the device
+ * passed to fds_init; "host" pointers are ordinary host memory.  The caller owns every
+ * buffer; the library never frees or retains caller memory.  Device buffers must be
+ * 16-byte aligned (pixels: 8-byte aligned).
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Kernels are enqueued
+ * asynchronously; argument errors are reported synchronously by the return value, errors
+ * of the enqueued work by the next call that synchronises (fds_sync) or by the CUDA
+ * runtime.
+ *
+ * Errors: every function returns FDS_OK (0) or a negative FDS_E_* code and never aborts or
+ * prints; fds_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef FDS_H
+#define FDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDS_OK 0
+#define FDS_E_INVALID (-1)  /* bad argument: size, alignment, k, null pointer, overflow */
+#define FDS_E_NO_KEY (-2)   /* key slot not registered */
+#define FDS_E_NOMEM (-3)    /* device or host allocation failed */
+#define FDS_E_CUDA (-4)     /* CUDA runtime error; see fds_last_error() */
+#define FDS_E_TIMEOUT (-5)  /* a bounded device wait gave up */
+#define FDS_E_BUSY (-6)     /* no capacity to admit the work now */
+
+#define FDS_MAX_KEYS 256
+
+/* One image of a batch.  Offsets are in bytes from the batch buffers passed to the call. */
+typedef struct fds_image {
+  uint64_t pixel_offset;   /* into the pixel buffer; multiple of 8 */
+  uint64_t public_offset;  /* into the public buffer; multiple of 16 */
+  uint64_t private_offset; /* into the private buffer; multiple of 16 */
+  int32_t width;           /* multiple of 8, >= 8 */
+  int32_t height;          /* multiple of 8, >= 8 */
+  int32_t k;               /* selection: zigzag positions 0..k are private, 0 <= k <= 63 */
+  int32_t key_slot;        /* a slot returned by fds_key_register */
+  uint8_t iv[16];          /* initial counter block of this image's private message */
+} fds_image;
+
+/* Select the CUDA device and build the library's device tables (AES tables, fixed-point
+ * constants of the exact rounding path).  Idempotent per device. */
+int fds_init(int device);
+
+/* Expand an AES-128 key (FIPS-197 Sect. 5.2) and keep its round keys resident on the
+ * device.  key: host, 16 bytes.  *slot_out receives the slot (0 .. FDS_MAX_KEYS-1).
+ * FDS_E_BUSY when every slot is taken. */
+int fds_key_register(const uint8_t key[16], int32_t* slot_out);
+
+/* Free a key slot.  Work already enqueued with the slot must have completed. */
+int fds_key_release(int32_t slot);
+
+/* Sizes in bytes of the public and private fragments of one width x height image at
+ * selection k: 2 (63 - k) and 2 (k + 1) bytes per channel-block.  Host pointers. */
+int fds_sizes(int32_t width, int32_t height, int32_t k, uint64_t* public_bytes,
+              uint64_t* private_bytes);
+
+/* Protect one image (Sect. 6.3.1).  pixels: device, H x W x 3 uint8.  key, iv: host, 16
+ * bytes each.  public_out, private_out: device, fds_sizes() bytes. */
+int fds_protect_image(const uint8_t* pixels, int32_t width, int32_t height, int32_t k,
+                      const uint8_t key[16], const uint8_t iv[16], int16_t* public_out,
+                      uint8_t* private_out, void* stream);
+
+/* Restore one image (inverse of fds_protect_image).  public_in, private_in: device.
+ * pixels_out: device, H x W x 3 uint8. */
+int fds_restore_image(const int16_t* public_in, const uint8_t* private_in, int32_t width,
+                      int32_t height, int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                      uint8_t* pixels_out, void* stream);
+
+/* Protect a batch of n images (descriptors: host array of n) whose pixels, public and
+ * private fragments live at the descriptors' offsets in three device buffers.  Keys are
+ * taken from registered slots.  One launch per image. */
+int fds_protect(const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
+                const fds_image* images, int32_t n, void* stream);
+
+/* Restore a batch (inverse of fds_protect). */
+int fds_restore(const int16_t* public_in, const uint8_t* private_in, uint8_t* pixels_out,
+                const fds_image* images, int32_t n, void* stream);
+
+/* Diagnostics: the float32 coefficients the protect kernel computes before rounding, as
+ * float [H/8][W/8][3][8][8] ([u][v] inside a block).  coefs_out: device.  Used to compare
+ * the pre-rounding values with a float64 reference (Sect. 6.4.3 precision concern). */
+int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
+                      float* coefs_out, void* stream);
+
+/* Diagnostics: counters of the exact-rounding fallbacks taken since the last reset,
+ * out[0] = values re-decided in 64-bit fixed point, out[1] = values decided in exact
+ * algebraic arithmetic, out[2] = internal consistency failures (must stay 0).
+ * Host pointer to 3 uint64.  Synchronises the device.  reset != 0 clears them. */
+int fds_counters(uint64_t* out, int reset);
+
+/* Wait for all work on `stream` and report any asynchronous CUDA error. */
+int fds_sync(void* stream);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* fds_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDS_H */

@@ -1,0 +1,171 @@
+"""Python binding of the C ABI: torch tensors in, torch tensors out.
+
+PyTorch provides device memory and the current CUDA stream; every step of protect and
+restore runs in the library's CUDA kernels.  Function names follow include/fds.h.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Sequence
+
+import torch
+
+from . import _lib
+
+
+def _stream_ptr(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _check_key(b: bytes, what: str) -> bytes:
+    b = bytes(b)
+    if len(b) != 16:
+        raise ValueError(f"{what} must be 16 bytes")
+    return b
+
+
+def init(device: int = 0) -> None:
+    """fds_init: select the device and build the library's device tables."""
+    _lib.check(_lib.load().fds_init(device), "fds_init")
+
+
+def sizes(width: int, height: int, k: int) -> tuple[int, int]:
+    """fds_sizes: (public bytes, private bytes) of one image."""
+    pub, priv = ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.check(_lib.load().fds_sizes(width, height, k, ctypes.byref(pub), ctypes.byref(priv)),
+               "fds_sizes")
+    return pub.value, priv.value
+
+
+def key_register(key: bytes) -> int:
+    """fds_key_register: keep an AES-128 key's round keys resident; returns its slot."""
+    slot = ctypes.c_int32()
+    _lib.check(_lib.load().fds_key_register(_check_key(key, "key"), ctypes.byref(slot)),
+               "fds_key_register")
+    return slot.value
+
+
+def key_release(slot: int) -> None:
+    _lib.check(_lib.load().fds_key_release(slot), "fds_key_release")
+
+
+def _image_dims(pixels: torch.Tensor) -> tuple[int, int]:
+    if pixels.dtype != torch.uint8 or pixels.dim() != 3 or pixels.shape[2] != 3:
+        raise ValueError("pixels must be an H x W x 3 uint8 tensor")
+    if not pixels.is_cuda or not pixels.is_contiguous():
+        raise ValueError("pixels must be a contiguous CUDA tensor")
+    return int(pixels.shape[1]), int(pixels.shape[0])
+
+
+def protect_image(pixels: torch.Tensor, key: bytes, iv: bytes, k: int,
+                  public_out: torch.Tensor | None = None,
+                  private_out: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """fds_protect_image: returns (public int16 [H/8, W/8, 3, 63-k], private uint8 bytes)."""
+    w, h = _image_dims(pixels)
+    pub_b, priv_b = sizes(w, h, k)
+    dev = pixels.device
+    if public_out is None:
+        public_out = torch.empty((h // 8, w // 8, 3, 63 - k), dtype=torch.int16, device=dev)
+    if private_out is None:
+        private_out = torch.empty(priv_b, dtype=torch.uint8, device=dev)
+    assert public_out.numel() * 2 == pub_b and private_out.numel() == priv_b
+    rc = _lib.load().fds_protect_image(
+        pixels.data_ptr(), w, h, k, _check_key(key, "key"), _check_key(iv, "iv"),
+        public_out.data_ptr() if public_out.numel() else None, private_out.data_ptr(),
+        _stream_ptr(dev))
+    _lib.check(rc, "fds_protect_image")
+    return public_out, private_out
+
+
+def restore_image(public: torch.Tensor, private: torch.Tensor, width: int, height: int, k: int,
+                  key: bytes, iv: bytes, pixels_out: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_restore_image: returns the H x W x 3 uint8 image."""
+    dev = private.device
+    if pixels_out is None:
+        pixels_out = torch.empty((height, width, 3), dtype=torch.uint8, device=dev)
+    rc = _lib.load().fds_restore_image(
+        public.data_ptr() if public.numel() else None, private.data_ptr(), width, height, k,
+        _check_key(key, "key"), _check_key(iv, "iv"), pixels_out.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_restore_image")
+    return pixels_out
+
+
+@dataclass
+class ImageDesc:
+    """One image of a batch (struct fds_image): byte offsets into the batch buffers."""
+    width: int
+    height: int
+    k: int
+    key_slot: int
+    iv: bytes
+    pixel_offset: int = 0
+    public_offset: int = 0
+    private_offset: int = 0
+
+
+def _align16(x: int) -> int:
+    return (x + 15) & ~15
+
+
+def layout(descs: Sequence[ImageDesc]) -> tuple[int, int, int]:
+    """Assign packed offsets (pixels 8-aligned, fragments 16-aligned) in place; returns the
+    (pixel, public, private) buffer sizes in bytes."""
+    px = pub = priv = 0
+    for d in descs:
+        pb, vb = sizes(d.width, d.height, d.k)
+        d.pixel_offset, d.public_offset, d.private_offset = px, pub, priv
+        px += (d.width * d.height * 3 + 7) & ~7
+        pub = _align16(pub + pb)
+        priv = _align16(priv + vb)
+    return px, pub, priv
+
+
+def _desc_array(descs: Sequence[ImageDesc]):
+    arr = (_lib.FdsImage * max(1, len(descs)))()
+    for i, d in enumerate(descs):
+        e = arr[i]
+        e.pixel_offset, e.public_offset, e.private_offset = d.pixel_offset, d.public_offset, d.private_offset
+        e.width, e.height, e.k, e.key_slot = d.width, d.height, d.k, d.key_slot
+        ctypes.memmove(e.iv, _check_key(d.iv, "iv"), 16)
+    return arr
+
+
+def protect(pixels: torch.Tensor, public_out: torch.Tensor, private_out: torch.Tensor,
+            descs: Sequence[ImageDesc]) -> None:
+    """fds_protect: a batch of images in three flat device buffers (uint8)."""
+    arr = _desc_array(descs)
+    rc = _lib.load().fds_protect(pixels.data_ptr(), public_out.data_ptr(), private_out.data_ptr(),
+                                 arr, len(descs), _stream_ptr(pixels.device))
+    _lib.check(rc, "fds_protect")
+
+
+def restore(public: torch.Tensor, private: torch.Tensor, pixels_out: torch.Tensor,
+            descs: Sequence[ImageDesc]) -> None:
+    """fds_restore: inverse of protect() for a batch."""
+    arr = _desc_array(descs)
+    rc = _lib.load().fds_restore(public.data_ptr(), private.data_ptr(), pixels_out.data_ptr(),
+                                 arr, len(descs), _stream_ptr(pixels_out.device))
+    _lib.check(rc, "fds_restore")
+
+
+def debug_dct_f32(pixels: torch.Tensor) -> torch.Tensor:
+    """fds_debug_dct_f32: float32 coefficients [H/8, W/8, 3, 8, 8] before rounding."""
+    w, h = _image_dims(pixels)
+    out = torch.empty((h // 8, w // 8, 3, 8, 8), dtype=torch.float32, device=pixels.device)
+    rc = _lib.load().fds_debug_dct_f32(pixels.data_ptr(), w, h, out.data_ptr(),
+                                       _stream_ptr(pixels.device))
+    _lib.check(rc, "fds_debug_dct_f32")
+    return out
+
+
+def counters(reset: bool = False) -> tuple[int, int, int]:
+    """fds_counters: (fixed-point re-decisions, exact-arithmetic decisions, failures)."""
+    out = (ctypes.c_uint64 * 3)()
+    _lib.check(_lib.load().fds_counters(out, 1 if reset else 0), "fds_counters")
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def sync() -> None:
+    """fds_sync on the current stream."""
+    _lib.check(_lib.load().fds_sync(_stream_ptr(torch.device("cuda"))), "fds_sync")

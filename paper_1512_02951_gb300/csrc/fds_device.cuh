@@ -1,0 +1,266 @@
+// Device building blocks of the selective-protection kernels (sm_103a).
+//
+//  * 8-point DCT-II / inverse butterflies in float32 (Sect. 6.4.2: separable 8x8 transform)
+//  * AES-128 with one T-table in shared memory and CTR counter blocks (FIPS-197; Sect. 6.12)
+//  * the exact-rounding fallback (Sect. 6.4.3 reading: round half away from zero of the exact
+//    value): a 64-bit fixed-point re-evaluation, then exact arithmetic in Z[cos(pi/16)]
+#pragma once
+
+#include <stdint.h>
+
+#include "fds_cos_limbs.h"
+
+namespace fds {
+
+// ------------------------------------------------------------------------------------------
+// constants
+// cos(j pi / 16)
+constexpr double kC1 = 0.98078528040323044912618223613424;
+constexpr double kC2 = 0.92387953251128675612818318939679;
+constexpr double kC3 = 0.83146961230254523707878837761791;
+constexpr double kC5 = 0.55557023301960222474283081394853;
+constexpr double kC6 = 0.38268343236508977172845998403040;
+constexpr double kC7 = 0.19509032201612826784828486847702;
+constexpr double kLambda = 0.35355339059327376220042218105242;  // 1 / (2 sqrt 2) = b_0
+
+// 2^23 + 2^22: adding it to a float of magnitude < 2^22 rounds to an integer (to nearest,
+// ties to even) that sits in the low mantissa bits.
+constexpr float kMagic = 12582912.0f;
+constexpr int kMagicBits = 0x4B400000;
+
+// zigzag scan position of (u, v): anti-diagonals s = u + v; odd s walks u upward from its
+// smallest value, even s downward from its largest.
+__host__ __device__ constexpr int zigzag_of(int u, int v) {
+  int z = 0;
+  for (int s = 0; s < 15; ++s) {
+    int lo = s > 7 ? s - 7 : 0, hi = s < 7 ? s : 7;
+    if (s != u + v) {
+      z += hi - lo + 1;
+      continue;
+    }
+    return (s & 1) ? z + (u - lo) : z + (hi - u);
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------------------------------
+// 8-point butterflies.  All constants are products computed in double and rounded once.
+//
+// Forward: x -> X with X_k = sum_n b_k(n) x_n for k in {1, 2, 3, 5, 6, 7} (times `irr`), and
+// X_0 = sum_n x_n, X_4 = sum_n w_n x_n (w = +1 -1 -1 +1 +1 -1 -1 +1) left unscaled when
+// RAT_UNSCALED, else multiplied by b_0 = 1/(2 sqrt 2).  Unscaled rational outputs of integer
+// inputs are exact, which keeps F[0][0], F[0][4], F[4][0], F[4][4] exact (each is an
+// integer / 8).
+template <bool RAT_UNSCALED, bool IRR_LAMBDA>
+__device__ __forceinline__ void dct8(float (&x)[8]) {
+  constexpr double m = IRR_LAMBDA ? kLambda : 1.0;
+  constexpr float a2 = (float)(0.5 * m * kC2), a6 = (float)(0.5 * m * kC6);
+  constexpr float h1 = (float)(0.5 * m * kC1), h3 = (float)(0.5 * m * kC3);
+  constexpr float h5 = (float)(0.5 * m * kC5), h7 = (float)(0.5 * m * kC7);
+  constexpr float lam = (float)kLambda;
+  const float s0 = x[0] + x[7], s1 = x[1] + x[6], s2 = x[2] + x[5], s3 = x[3] + x[4];
+  const float d0 = x[0] - x[7], d1 = x[1] - x[6], d2 = x[2] - x[5], d3 = x[3] - x[4];
+  const float e0 = s0 + s3, e1 = s1 + s2, f0 = s0 - s3, f1 = s1 - s2;
+  if (RAT_UNSCALED) {
+    x[0] = e0 + e1;
+    x[4] = e0 - e1;
+  } else {
+    x[0] = fmaf(e0, lam, e1 * lam);
+    x[4] = fmaf(e0, lam, e1 * -lam);
+  }
+  x[2] = fmaf(f0, a2, f1 * a6);
+  x[6] = fmaf(f0, a6, f1 * -a2);
+  // odd rows of the basis on d_n = x_n - x_(7-n), n = 0..3
+  x[1] = fmaf(d3, h7, fmaf(d2, h5, fmaf(d1, h3, d0 * h1)));
+  x[3] = fmaf(d3, -h5, fmaf(d2, -h1, fmaf(d1, -h7, d0 * h3)));
+  x[5] = fmaf(d3, h3, fmaf(d2, h7, fmaf(d1, -h1, d0 * h5)));
+  x[7] = fmaf(d3, -h1, fmaf(d2, h3, fmaf(d1, -h5, d0 * h7)));
+}
+
+// Inverse: X (orthonormal coefficients) -> x_n = sum_k b_k(n) X_k.
+__device__ __forceinline__ void idct8(float (&x)[8]) {
+  constexpr float lam = (float)kLambda;
+  constexpr float c2 = (float)(0.5 * kC2), c6 = (float)(0.5 * kC6);
+  constexpr float h1 = (float)(0.5 * kC1), h3 = (float)(0.5 * kC3);
+  constexpr float h5 = (float)(0.5 * kC5), h7 = (float)(0.5 * kC7);
+  const float a = fmaf(x[0], lam, x[4] * lam), b = fmaf(x[0], lam, x[4] * -lam);
+  const float t1 = fmaf(x[2], c2, x[6] * c6), t2 = fmaf(x[2], c6, x[6] * -c2);
+  const float e0 = a + t1, e1 = b + t2, e2 = b - t2, e3 = a - t1;
+  const float o0 = fmaf(x[7], h7, fmaf(x[5], h5, fmaf(x[3], h3, x[1] * h1)));
+  const float o1 = fmaf(x[7], -h5, fmaf(x[5], -h1, fmaf(x[3], -h7, x[1] * h3)));
+  const float o2 = fmaf(x[7], h3, fmaf(x[5], h7, fmaf(x[3], -h1, x[1] * h5)));
+  const float o3 = fmaf(x[7], -h1, fmaf(x[5], h3, fmaf(x[3], -h5, x[1] * h7)));
+  x[0] = e0 + o0;
+  x[7] = e0 - o0;
+  x[1] = e1 + o1;
+  x[6] = e1 - o1;
+  x[2] = e2 + o2;
+  x[5] = e2 - o2;
+  x[3] = e3 + o3;
+  x[4] = e3 - o3;
+}
+
+// ------------------------------------------------------------------------------------------
+// AES-128 (FIPS-197).  A state column is a 32-bit word holding bytes 4c .. 4c+3 of the block
+// little-endian (byte r of the column at bits 8r); round keys use the same word convention.
+
+__host__ __device__ inline uint8_t gf_xtime(uint8_t a) {
+  return (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1B : 0x00));
+}
+
+__host__ __device__ inline uint8_t gf_mul(uint8_t a, uint8_t b) {
+  uint8_t r = 0;
+  for (int i = 0; i < 8; ++i) {
+    if (b & 1) r ^= a;
+    a = gf_xtime(a);
+    b >>= 1;
+  }
+  return r;
+}
+
+// S-box entry from its definition: inverse in GF(2^8) (x^254, 0 -> 0), then the affine map
+// b ^ rotl(b,1) ^ rotl(b,2) ^ rotl(b,3) ^ rotl(b,4) ^ 0x63.
+__host__ __device__ inline uint8_t aes_sbox(uint8_t x) {
+  uint8_t inv = 1, p = gf_mul(x, x);
+  for (int i = 0; i < 7; ++i) {
+    inv = gf_mul(inv, p);
+    p = gf_mul(p, p);
+  }
+  if (x == 0) inv = 0;
+  uint8_t r = 0x63;
+  for (int k = 0; k < 5; ++k) r ^= (uint8_t)((inv << k) | (inv >> ((8 - k) & 7)));
+  return r;
+}
+
+// T0[x] = (2S, S, S, 3S) as bytes 0..3: the MixColumns column of S[x] in row 0.
+__host__ __device__ inline uint32_t aes_t0(uint8_t x) {
+  uint8_t s = aes_sbox(x), s2 = gf_xtime(s), s3 = (uint8_t)(s2 ^ s);
+  return (uint32_t)s2 | ((uint32_t)s << 8) | ((uint32_t)s << 16) | ((uint32_t)s3 << 24);
+}
+
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int n) { return __funnelshift_l(x, x, n); }
+
+// S[x] moved to byte position `pos` of a word; T0[x] holds S[x] in byte 1.
+template <int POS>
+__device__ __forceinline__ uint32_t sbox_at(const uint32_t* T0, uint32_t idx) {
+  uint32_t t = T0[idx];
+  // __byte_perm(t, 0, sel): result byte POS = t byte 1, others = 0 (selector 4 = zero byte)
+  constexpr uint32_t sel = (POS == 0) ? 0x4441u : (POS == 1) ? 0x4414u : (POS == 2) ? 0x4144u : 0x1444u;
+  return __byte_perm(t, 0u, sel);
+}
+
+// Encrypt one block in place.  rk: 44 round-key words; T0: shared-memory table.
+__device__ __forceinline__ void aes128_encrypt(uint32_t (&s)[4], const uint32_t* rk,
+                                               const uint32_t* T0) {
+  uint32_t s0 = s[0] ^ rk[0], s1 = s[1] ^ rk[1], s2 = s[2] ^ rk[2], s3 = s[3] ^ rk[3];
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t t0 = T0[s0 & 0xff] ^ rotl32(T0[(s1 >> 8) & 0xff], 8) ^
+                        rotl32(T0[(s2 >> 16) & 0xff], 16) ^ rotl32(T0[s3 >> 24], 24) ^ rk[4 * r];
+    const uint32_t t1 = T0[s1 & 0xff] ^ rotl32(T0[(s2 >> 8) & 0xff], 8) ^
+                        rotl32(T0[(s3 >> 16) & 0xff], 16) ^ rotl32(T0[s0 >> 24], 24) ^ rk[4 * r + 1];
+    const uint32_t t2 = T0[s2 & 0xff] ^ rotl32(T0[(s3 >> 8) & 0xff], 8) ^
+                        rotl32(T0[(s0 >> 16) & 0xff], 16) ^ rotl32(T0[s1 >> 24], 24) ^ rk[4 * r + 2];
+    const uint32_t t3 = T0[s3 & 0xff] ^ rotl32(T0[(s0 >> 8) & 0xff], 8) ^
+                        rotl32(T0[(s1 >> 16) & 0xff], 16) ^ rotl32(T0[s2 >> 24], 24) ^ rk[4 * r + 3];
+    s0 = t0;
+    s1 = t1;
+    s2 = t2;
+    s3 = t3;
+  }
+  s[0] = sbox_at<0>(T0, s0 & 0xff) | sbox_at<1>(T0, (s1 >> 8) & 0xff) |
+         sbox_at<2>(T0, (s2 >> 16) & 0xff) | sbox_at<3>(T0, s3 >> 24);
+  s[1] = sbox_at<0>(T0, s1 & 0xff) | sbox_at<1>(T0, (s2 >> 8) & 0xff) |
+         sbox_at<2>(T0, (s3 >> 16) & 0xff) | sbox_at<3>(T0, s0 >> 24);
+  s[2] = sbox_at<0>(T0, s2 & 0xff) | sbox_at<1>(T0, (s3 >> 8) & 0xff) |
+         sbox_at<2>(T0, (s0 >> 16) & 0xff) | sbox_at<3>(T0, s1 >> 24);
+  s[3] = sbox_at<0>(T0, s3 & 0xff) | sbox_at<1>(T0, (s0 >> 8) & 0xff) |
+         sbox_at<2>(T0, (s1 >> 16) & 0xff) | sbox_at<3>(T0, s2 >> 24);
+  s[0] ^= rk[40];
+  s[1] ^= rk[41];
+  s[2] ^= rk[42];
+  s[3] ^= rk[43];
+}
+
+// Counter block IV + n (128-bit big-endian addition) as four state columns.
+// iv_hi / iv_lo: the IV's bytes 0..7 / 8..15 read as big-endian integers.
+__device__ __forceinline__ void ctr_block(uint64_t iv_hi, uint64_t iv_lo, uint64_t n,
+                                          uint32_t (&s)[4]) {
+  const uint64_t lo = iv_lo + n;
+  const uint64_t hi = iv_hi + (lo < n ? 1ull : 0ull);
+  s[0] = __byte_perm((uint32_t)(hi >> 32), 0u, 0x0123);
+  s[1] = __byte_perm((uint32_t)hi, 0u, 0x0123);
+  s[2] = __byte_perm((uint32_t)(lo >> 32), 0u, 0x0123);
+  s[3] = __byte_perm((uint32_t)lo, 0u, 0x0123);
+}
+
+// ------------------------------------------------------------------------------------------
+// Exact decision for values near a rounding boundary.
+//
+// With c(m) = cos(m pi/16): 8 b_u(y) b_v(x) = c(a-b) + c(a+b), a = 4 if u == 0 else
+// (2y+1)u, b = 4 if v == 0 else (2x+1)v.  So 8 F[u][v] of an integer block, and 8 p[y][x] of
+// an integer coefficient block, are N_0 + sum_{j=1..7} N_j c(j) with integers N_j, and the
+// side of a half-integer h is the sign of (N_0 - 8h) + sum N_j c(j).
+
+// cos(j pi/16), j = 1..7, to 256 fractional bits (each translation unit holds its own copy)
+static __constant__ uint32_t c_cos_limbs[7][8] = FDS_COS_LIMBS_INIT;
+
+// fold c(m) to +-c(j): accumulate `val` into coordinate j of acc (c(8) = 0 is dropped)
+__device__ __forceinline__ void add_cos_term(int (&acc)[9], int m, int val) {
+  m &= 31;
+  if (m > 16) m = 32 - m;
+  if (m > 8)
+    acc[16 - m] -= val;
+  else
+    acc[m] += val;
+}
+
+// Sign of a0 + sum_{j=1..7} n[j] c(j), evaluated with c(j) to 256 fractional bits.
+// A nonzero value of this form has modulus >= 1 / (2 (2|a0| + 2 sum|n|)^7) (2 c(j) are
+// algebraic integers, the field has degree 8, every conjugate is at most 2|a0| + 2 sum|n|),
+// far above the evaluation error for |a0|, sum|n| < 2^26.  Returns +1 / -1, 0 for an exact
+// zero; *fail is set if the fixed-point value lands inside its error bound although the
+// irrational part is nonzero (impossible by the bound above).
+__device__ inline int exact_sign(int a0, const int (&n)[9], bool* fail) {
+  int any = 0;
+  long long err = 0;
+#pragma unroll
+  for (int j = 1; j < 8; ++j) {
+    any |= n[j];
+    err += 2ll * (n[j] < 0 ? -(long long)n[j] : (long long)n[j]);
+  }
+  if (!any) return (a0 > 0) - (a0 < 0);
+  uint32_t L[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) L[i] = 0;
+  long long top = a0;
+  for (int j = 1; j < 8; ++j) {
+    const long long nj = n[j];
+    long long carry = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const long long t = (long long)L[i] + nj * (long long)c_cos_limbs[j - 1][i] + carry;
+      L[i] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    top += carry;
+  }
+  // D = top * 2^256 + sum L[i] 2^(32 i), |D - value * 2^256| <= err (< 2^32)
+  if (top > 0) return 1;
+  if (top < -1) return -1;
+  uint32_t mid = 0;
+  if (top == 0) {
+#pragma unroll
+    for (int i = 1; i < 8; ++i) mid |= L[i];
+    if (mid || (long long)L[0] > err) return 1;
+  } else {  // top == -1: D = L - 2^256
+    uint32_t all = 0xffffffffu;
+#pragma unroll
+    for (int i = 1; i < 8; ++i) all &= L[i];
+    if (all != 0xffffffffu || (long long)(0xffffffffu - L[0]) + 1 > err) return -1;
+  }
+  *fail = true;
+  return 1;
+}
+
+}  // namespace fds

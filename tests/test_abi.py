@@ -1,0 +1,101 @@
+"""The C-ABI library: it builds, loads, exports every symbol of include/fds.h, and its host-side
+logic (sizes, argument checks, key registry) behaves without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+from oracle import exact, fds as ofds
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1512_02951_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "fds.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(fds_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1512_02951_gb300 import _lib
+
+    names = _declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.SIGNATURES), "binding and header disagree"
+
+
+def test_struct_layout_matches_header():
+    from paper_1512_02951_gb300 import _lib
+
+    assert ctypes.sizeof(_lib.FdsImage) == 56
+    assert _lib.FdsImage.iv.offset == 40
+
+
+@pytest.mark.parametrize("w,h,k", [(512, 512, 0), (4096, 4096, 5), (64, 8, 63), (8, 8, 17)])
+def test_sizes_match_oracle(lib, w, h, k):
+    pub, priv = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.fds_sizes(w, h, k, ctypes.byref(pub), ctypes.byref(priv)) == 0
+    assert (pub.value, priv.value) == ofds.sizes(w, h, k)
+
+
+@pytest.mark.parametrize("w,h,k", [(100, 64, 0), (64, 0, 0), (-8, 64, 0), (64, 64, 64), (64, 64, -1)])
+def test_invalid_arguments_are_rejected_on_the_host(lib, w, h, k):
+    pub, priv = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.fds_sizes(w, h, k, ctypes.byref(pub), ctypes.byref(priv)) == -1
+    assert lib.fds_last_error()
+    key = bytes(16)
+    rc = lib.fds_protect_image(None, w, h, k, key, key, None, None, None)
+    assert rc == -1
+
+
+def test_null_and_misaligned_pointers_are_rejected(lib):
+    key = bytes(16)
+    assert lib.fds_protect_image(None, 64, 64, 0, key, key, 16, 16, None) == -1
+    assert lib.fds_protect_image(8, 64, 64, 0, key, key, 24, 16, None) == -1   # public not 16-aligned
+    assert b"aligned" in lib.fds_last_error()
+
+
+def test_key_registry(lib):
+    slots = []
+    slot = ctypes.c_int32()
+    for _ in range(256):
+        assert lib.fds_key_register(bytes(range(16)), ctypes.byref(slot)) == 0
+        slots.append(slot.value)
+    assert sorted(slots) == list(range(256))
+    assert lib.fds_key_register(bytes(16), ctypes.byref(slot)) == -6          # all slots taken
+    for s in slots:
+        assert lib.fds_key_release(s) == 0
+    assert lib.fds_key_release(3) == -2                                        # already free
+
+
+def test_device_cosine_constants_agree_with_the_oracle():
+    # the CUDA path's 256-bit cosines come from a Taylor-series generator; the oracle's from
+    # nested integer square roots.  Both must give the same numbers.
+    path = os.path.join(ROOT, "paper_1512_02951_gb300", "csrc", "fds_cos_limbs.h")
+    words = [int(x, 16) for x in re.findall(r"0x([0-9a-f]{8})u", open(path).read())]
+    assert len(words) == 56
+    for j in range(7):
+        limbs = words[8 * j: 8 * j + 8]
+        dev = sum(l << (32 * i) for i, l in enumerate(limbs))
+        ora = exact.COS_FIXED[j + 1] >> (exact.FRAC_BITS - 256)
+        assert abs(dev - ora) <= 2
+
+
+def test_generated_header_is_up_to_date():
+    import subprocess
+    import sys
+
+    csrc = os.path.join(ROOT, "paper_1512_02951_gb300", "csrc")
+    out = subprocess.run([sys.executable, os.path.join(csrc, "gen_cos_limbs.py")],
+                         capture_output=True, text=True, check=True).stdout
+    assert out == open(os.path.join(csrc, "fds_cos_limbs.h")).read()
