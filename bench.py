@@ -1,0 +1,396 @@
+"""Benchmark: protect + restore of one 4096 x 4096 RGB uint8 image per GPU, k = 5.
+
+One step = the whole hot path on one image: the fused protect kernel (8x8 DCT-II, exact int16
+rounding, zigzag split, AES-128-CTR of the confidential fragment) followed by the fused
+restore kernel (CTR decryption, merge, inverse DCT, exact rounding, clamp).  The metric is MB/s
+of input pixels (W * H * 3 bytes per step / step time, 10^6 bytes per MB); ranks run
+independent images (weak scaling, no collective on the data path).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead, on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WIDTH = HEIGHT = 4096
+K_SEL = 5
+IMG_SEED, KEY_SEED, IV_SEED = 2, 2005, 3005
+METRIC = "protect+restore MB/s of pixels"
+UNIT = "MB/s"
+WORKLOAD = f"{WIDTH}x{HEIGHT} RGB uint8, protect+restore, k={K_SEL}"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _config():
+    return {"workload": WORKLOAD, "width": WIDTH, "height": HEIGHT, "k": K_SEL,
+            "channels": 3, "generator": "20 random 2-D Gaussians + U[-8,8] noise, seed 2",
+            "l2": "inputs larger than L2: two fragment buffer sets alternate, so restore reads "
+                  "fragments written one step earlier (>= 250 MB of traffic since)"}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+def _oracle_child(args):
+    """Runs in a child process with one BLAS/OpenMP thread: oracle protect + restore on
+    strips of the workload image until `args.budget` seconds are used."""
+    import numpy as np
+
+    from oracle import aes as oaes, dct as odct, fds as ofds
+    from paper_1512_02951_gb300 import synth
+
+    img = synth.make_image(WIDTH, HEIGHT, IMG_SEED)
+    key, iv = synth.make_key(KEY_SEED), synth.make_iv(IV_SEED)
+    rows = args.rows
+    bx = WIDTH // 8
+    done_bytes, t_used, times = 0, 0.0, []
+    r0 = 0
+    while r0 < HEIGHT // 8 and (t_used < args.budget or not times) and len(times) < args.max_steps:
+        r1 = min(HEIGHT // 8, r0 + rows)
+        strip = img[8 * r0: 8 * r1]
+        t = time.perf_counter()
+        q, _ = ofds.quantised_dct(odct.image_to_blocks(strip))
+        part1, part2 = ofds.split(q.astype(np.int16), K_SEL)
+        off = r0 * bx * 3 * 2 * (K_SEL + 1)
+        ct = oaes.ctr_xcrypt(key, iv, np.ascontiguousarray(part1).astype("<i2").tobytes(), offset=off)
+        plain = oaes.ctr_xcrypt(key, iv, ct, offset=off)
+        p1 = np.frombuffer(plain, dtype="<i2").astype(np.int64).reshape(part1.shape)
+        p = ofds.quantised_idct(ofds.merge(p1, part2.astype(np.int64)))
+        back = odct.blocks_to_image(np.clip(p, 0, 255).astype(np.uint8))
+        dt = time.perf_counter() - t
+        assert back.shape == strip.shape
+        times.append(dt)
+        t_used += dt
+        done_bytes += strip.nbytes
+        r0 = r1 if r1 < HEIGHT // 8 else 0
+    print(json.dumps({"bytes": done_bytes, "seconds": t_used, "steps": len(times),
+                      "rows_per_step": rows, "times": times}))
+
+
+def _run_oracle(rows, budget, max_steps):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--rows", str(rows),
+           "--budget", str(budget), "--max-steps", str(max_steps)]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, check=True).stdout
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    r = _run_oracle(rows=32, budget=20.0, max_steps=10 ** 6)
+    mbps = r["bytes"] / r["seconds"] / 1e6
+    return {"value": round(mbps, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{r['steps']} strips of {r['rows_per_step']} block rows "
+                      f"({r['bytes'] / 1e6:.1f} MB of pixels) of the workload image, "
+                      "float64 numpy oracle, one thread"}
+
+
+def reference_arm(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    # size each step so that warmup + steps stay within about two minutes
+    probe = _run_oracle(rows=1, budget=0.0, max_steps=1)
+    per_row = max(probe["seconds"], 1e-3)
+    rows = int(max(1, min(64, 120.0 / ((args.steps + args.warmup) * per_row))))
+    r = _run_oracle(rows=rows, budget=1e9, max_steps=args.steps + args.warmup)
+    times = r["times"][args.warmup:] or r["times"]
+    step_bytes = rows * 8 * WIDTH * 3
+    ms = 1e3 * sum(times) / len(times)
+    value = step_bytes / (sum(times) / len(times)) / 1e6
+    sample = f"each step: {rows} block rows ({step_bytes / 1e6:.3f} MB) of the workload image"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+            "n_gpus": world, "steps": len(times), "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(),
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm helpers
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_02951_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current
+    kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_4096_k{K_SEL}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    tr = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not sha or not tr or sha.group(1) != _kernel_source_sha():
+        return None
+    return int(tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_index):
+        import torch
+        self.sel = []
+        try:
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            self.sel = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"] + self.sel, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for ln in (self.out or "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+
+    from paper_1512_02951_gb300 import api, build, synth
+
+    build.build()
+    api.init(local)
+    img_np = synth.make_image(WIDTH, HEIGHT, IMG_SEED + rank)
+    key, iv = synth.make_key(KEY_SEED + rank), synth.make_iv(IV_SEED + rank)
+    img = torch.from_numpy(img_np).to(dev)
+    pub_b, priv_b = api.sizes(WIDTH, HEIGHT, K_SEL)
+    sets = [(torch.empty((HEIGHT // 8, WIDTH // 8, 3, 63 - K_SEL), dtype=torch.int16, device=dev),
+             torch.empty(priv_b, dtype=torch.uint8, device=dev)) for _ in range(2)]
+    out = torch.empty_like(img)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i, ev=None):
+        pub, priv = sets[i % 2]
+        opub, opriv = sets[(i + 1) % 2]
+        if ev is not None:
+            ev[0].record(stream)
+        api.protect_image(img, key, iv, K_SEL, pub, priv)
+        if ev is not None:
+            ev[1].record(stream)
+        api.restore_image(opub, opriv, WIDTH, HEIGHT, K_SEL, key, iv, out)
+        if ev is not None:
+            ev[2].record(stream)
+
+    # correctness of what is timed: fragments and restored image of this very configuration
+    api.counters(reset=True)
+    step(0)
+    step(1)
+    torch.cuda.synchronize()
+    back = out.cpu().numpy()
+    exact_frac = float(np.mean(back == img_np))
+    mse = float(np.mean((back.astype(np.float64) - img_np) ** 2))
+    psnr = float("inf") if mse == 0 else 10 * np.log10(255.0 ** 2 / mse)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            step(i, evs[i])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = start.elapsed_time(stop)
+    prot_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    rest_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = sorted(a + b for a, b in zip(prot_ms, rest_ms))
+    n2, n3, fails = api.counters()
+
+    # end to end through the public API from pinned host memory
+    host_px = torch.from_numpy(img_np).pin_memory()
+    host_pub = torch.empty(sets[0][0].shape, dtype=torch.int16).pin_memory()
+    host_priv = torch.empty(priv_b, dtype=torch.uint8).pin_memory()
+    host_out = torch.empty(img_np.shape, dtype=torch.uint8).pin_memory()
+    dpx = torch.empty_like(img)
+    e2e_steps = max(1, min(args.steps, 200))
+
+    def e2e_step(i):
+        pub, priv = sets[i % 2]
+        dpx.copy_(host_px, non_blocking=True)
+        api.protect_image(dpx, key, iv, K_SEL, pub, priv)
+        host_pub.copy_(pub, non_blocking=True)
+        host_priv.copy_(priv, non_blocking=True)
+        api.restore_image(pub, priv, WIDTH, HEIGHT, K_SEL, key, iv, out)
+        host_out.copy_(out, non_blocking=True)
+
+    for i in range(3):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    assert np.array_equal(host_out.numpy(), back)
+
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+
+    px_bytes = WIDTH * HEIGHT * 3
+    ms_per_step = total_ms / args.steps
+    value = world * px_bytes / (ms_per_step * 1e-3) / 1e6
+    alg_bytes = px_bytes + pub_b + priv_b          # per launch, protect and restore alike
+    peak, peak_kind = _peaks()
+    prot_avg, rest_avg = sum(prot_ms) / len(prot_ms), sum(rest_ms) / len(rest_ms)
+    kern = {}
+    for name, ms in (("protect", prot_avg), ("restore", rest_avg)):
+        gbs = alg_bytes / (ms * 1e-3) / 1e9
+        kern[name] = {"ms": round(ms, 5), "alg_bytes": alg_bytes, "achieved_gbs": round(gbs, 1),
+                      "frac": round(gbs / peak, 4)}
+    dom = "protect" if prot_avg >= rest_avg else "restore"
+    roof = {"bound": "hbm", "achieved": kern[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kern[dom]["frac"], "traffic": _profiled_traffic(dom + "_kernel"),
+            "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(),
+            "latency_ms": {"p50": round(step_ms[len(step_ms) // 2], 5),
+                           "p99": round(step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 5)},
+            "roofline": roof, "kernels": kern,
+            "e2e": {"value": round(world * px_bytes / (e2e_ms * 1e-3) / 1e6, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": px_bytes,
+                    "d2h_bytes_per_step": pub_b + priv_b + px_bytes,
+                    "note": "H2D pixels, protect, D2H both fragments, restore, D2H pixels"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "quality": {"exact_restore_fraction": round(exact_frac, 5), "psnr_db": round(psnr, 3),
+                        "fixed_point_redecisions": n2, "exact_decisions": n3, "failures": fails},
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--rows", type=int, default=32, help=argparse.SUPPRESS)
+    ap.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
+    ap.add_argument("--max-steps", type=int, default=10 ** 6, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.oracle_child:
+        _oracle_child(args)
+    elif args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()
