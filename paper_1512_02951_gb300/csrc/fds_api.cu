@@ -13,15 +13,27 @@
 
 namespace fds {
 
-// device tables: AES T-table, stage-2 fixed-point DCT basis tables, fallback counters
-__device__ uint32_t g_T0[256];
-__device__ int32_t g_bfwd[64 * 64];
-__device__ int32_t g_binv[64 * 64];
+// Device tables (static, no allocation):
+//  g_T        AES T-tables T[r][x] = rotl(T0[x], 8r), r = 0..3
+//  g_cfwd     exact-coordinate weights of the forward transform: for coefficient 8u+v and
+//             coordinate j, 64 signed bytes K_j(u,v,y,x) (16 words, word w = row w/2,
+//             x = 4(w&1) .. +3)
+//  g_cinv     the same for the inverse: for pixel 8y+x and coordinate j, the weight of the
+//             coefficient at zigzag index z = 4t + byte (16 words)
+//  g_counters exact-fallback counters
+// where 8 b_u(y) b_v(x) = sum_j K_j(u,v,y,x) cos(j pi/16), cos(0) = 1.
+__device__ __align__(16) uint32_t g_T[1024];
+__device__ __align__(16) uint32_t g_cfwd[64 * 128];
+__device__ __align__(16) uint32_t g_cinv[64 * 128];
 __device__ unsigned long long g_counters[3];
 
 __global__ void init_tables_kernel() {
   const int t = threadIdx.x;
-  g_T0[t] = aes_t0((uint8_t)t);
+  const uint32_t t0 = aes_t0((uint8_t)t);
+  g_T[t] = t0;
+  g_T[256 + t] = (t0 << 8) | (t0 >> 24);
+  g_T[512 + t] = (t0 << 16) | (t0 >> 16);
+  g_T[768 + t] = (t0 << 24) | (t0 >> 8);
   if (t < 3) g_counters[t] = 0;
 }
 
@@ -34,10 +46,11 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 bool g_ready[kMaxDevices];
 struct DevTables {
-  const uint32_t* T0;
-  const int32_t* bfwd;
-  const int32_t* binv;
+  const uint32_t* T;
+  const uint32_t* cfwd;
+  const uint32_t* cinv;
   unsigned long long* counters;
+  int sms;
 };
 DevTables g_tables[kMaxDevices];
 
@@ -91,36 +104,69 @@ int ensure_init(int* dev_out = nullptr) {
   if (dev_out) *dev_out = dev;
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_ready[dev]) return FDS_OK;
-  // stage-2 tables in double precision: round(8 b_u(y) b_v(x) 2^28)
-  static int32_t hf[64 * 64], hi[64 * 64];
-  uint8_t zz[64];
-  for (int u = 0; u < 8; ++u)
-    for (int v = 0; v < 8; ++v) zz[8 * u + v] = (uint8_t)zigzag_of(u, v);
-  const double pi = 3.14159265358979323846264338327950288;
-  auto basis = [&](int u, int y) {
-    return (u == 0 ? std::sqrt(0.125) : 0.5) * std::cos((2 * y + 1) * u * pi / 16.0);
+  // exact-coordinate tables: fold cos(m pi/16) to +-cos(j pi/16), j = 0..8 (cos(8 pi/16) = 0)
+  auto fold = [](int m, int* j, int* sgn) {
+    m &= 31;
+    if (m > 16) m = 32 - m;
+    *sgn = 1;
+    if (m > 8) {
+      m = 16 - m;
+      *sgn = -1;
+    }
+    *j = m;
   };
+  static int8_t K[8][8][8][8][8];  // [u][v][y][x][j]
+  std::memset(K, 0, sizeof(K));
   for (int u = 0; u < 8; ++u)
     for (int v = 0; v < 8; ++v)
       for (int y = 0; y < 8; ++y)
         for (int x = 0; x < 8; ++x) {
-          const int32_t val = (int32_t)std::llround(8.0 * basis(u, y) * basis(v, x) * (double)(1 << kFixShift));
-          hf[(8 * u + v) * 64 + 8 * y + x] = val;
-          hi[(8 * y + x) * 64 + zz[8 * u + v]] = val;
+          const int al = u == 0 ? 4 : (2 * y + 1) * u, be = v == 0 ? 4 : (2 * x + 1) * v;
+          for (int m : {al - be, al + be}) {
+            int j, sg;
+            fold(m, &j, &sg);
+            if (j < 8) K[u][v][y][x][j] = (int8_t)(K[u][v][y][x][j] + sg);
+          }
         }
-  if ((e = cudaMemcpyToSymbol(g_bfwd, hf, sizeof(hf))) != cudaSuccess) return cuda_fail(e, "table upload");
-  if ((e = cudaMemcpyToSymbol(g_binv, hi, sizeof(hi))) != cudaSuccess) return cuda_fail(e, "table upload");
+  static uint32_t hf[64 * 128], hinv[64 * 128];
+  std::memset(hf, 0, sizeof(hf));
+  std::memset(hinv, 0, sizeof(hinv));
+  int uz[64], vz[64];
+  for (int u = 0; u < 8; ++u)
+    for (int v = 0; v < 8; ++v) {
+      uz[zigzag_of(u, v)] = u;
+      vz[zigzag_of(u, v)] = v;
+    }
+  for (int u = 0; u < 8; ++u)
+    for (int v = 0; v < 8; ++v)
+      for (int j = 0; j < 8; ++j)
+        for (int w = 0; w < 16; ++w)
+          for (int i = 0; i < 4; ++i)
+            hf[(8 * u + v) * 128 + 16 * j + w] |=
+                (uint32_t)(uint8_t)K[u][v][w >> 1][4 * (w & 1) + i][j] << (8 * i);
+  for (int y = 0; y < 8; ++y)
+    for (int x = 0; x < 8; ++x)
+      for (int j = 0; j < 8; ++j)
+        for (int tw = 0; tw < 16; ++tw)
+          for (int i = 0; i < 4; ++i) {
+            const int z = 4 * tw + i;
+            hinv[(8 * y + x) * 128 + 16 * j + tw] |= (uint32_t)(uint8_t)K[uz[z]][vz[z]][y][x][j] << (8 * i);
+          }
+  if ((e = cudaMemcpyToSymbol(g_cfwd, hf, sizeof(hf))) != cudaSuccess) return cuda_fail(e, "table upload");
+  if ((e = cudaMemcpyToSymbol(g_cinv, hinv, sizeof(hinv))) != cudaSuccess) return cuda_fail(e, "table upload");
   init_tables_kernel<<<1, 256>>>();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "init kernel launch");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "init kernel");
   DevTables& tb = g_tables[dev];
   void* p = nullptr;
-  if ((e = cudaGetSymbolAddress(&p, g_T0)) != cudaSuccess) return cuda_fail(e, "symbol address");
-  tb.T0 = static_cast<const uint32_t*>(p);
-  if ((e = cudaGetSymbolAddress(&p, g_bfwd)) != cudaSuccess) return cuda_fail(e, "symbol address");
-  tb.bfwd = static_cast<const int32_t*>(p);
-  if ((e = cudaGetSymbolAddress(&p, g_binv)) != cudaSuccess) return cuda_fail(e, "symbol address");
-  tb.binv = static_cast<const int32_t*>(p);
+  if ((e = cudaGetSymbolAddress(&p, g_T)) != cudaSuccess) return cuda_fail(e, "symbol address");
+  tb.T = static_cast<const uint32_t*>(p);
+  if ((e = cudaGetSymbolAddress(&p, g_cfwd)) != cudaSuccess) return cuda_fail(e, "symbol address");
+  tb.cfwd = static_cast<const uint32_t*>(p);
+  if ((e = cudaGetSymbolAddress(&p, g_cinv)) != cudaSuccess) return cuda_fail(e, "symbol address");
+  tb.cinv = static_cast<const uint32_t*>(p);
+  if ((e = cudaDeviceGetAttribute(&tb.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail(e, "device attribute");
   if ((e = cudaGetSymbolAddress(&p, g_counters)) != cudaSuccess) return cuda_fail(e, "symbol address");
   tb.counters = static_cast<unsigned long long*>(p);
   g_ready[dev] = true;
@@ -132,20 +178,20 @@ bool bad_dims(int32_t w, int32_t h) {
 }
 
 int run_protect(TileArgs& a, int dev, cudaStream_t s, bool debug) {
-  a.T0 = g_tables[dev].T0;
-  a.bfwd = g_tables[dev].bfwd;
-  a.binv = g_tables[dev].binv;
+  a.T = g_tables[dev].T;
+  a.cfwd = g_tables[dev].cfwd;
+  a.cinv = g_tables[dev].cinv;
   a.counters = g_tables[dev].counters;
-  const cudaError_t e = launch_protect(a, s, debug);
+  const cudaError_t e = launch_protect(a, s, debug, g_tables[dev].sms);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "protect launch");
 }
 
 int run_restore(TileArgs& a, int dev, cudaStream_t s) {
-  a.T0 = g_tables[dev].T0;
-  a.bfwd = g_tables[dev].bfwd;
-  a.binv = g_tables[dev].binv;
+  a.T = g_tables[dev].T;
+  a.cfwd = g_tables[dev].cfwd;
+  a.cinv = g_tables[dev].cinv;
   a.counters = g_tables[dev].counters;
-  const cudaError_t e = launch_restore(a, s);
+  const cudaError_t e = launch_restore(a, s, g_tables[dev].sms);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "restore launch");
 }
 

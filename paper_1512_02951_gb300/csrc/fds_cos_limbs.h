@@ -11,3 +11,6 @@
     {0x62718f71u, 0x3a3c1590u, 0xab3de24cu, 0xbdf1f5b4u, 0xcf7eee1bu, 0x98916152u, 0xbaa58b46u, 0x61f78a9au}, /* j = 6 */ \
     {0x895414c1u, 0x39438767u, 0x12972f1du, 0xf394e58du, 0x93f33613u, 0x97323003u, 0xd34c156cu, 0x31f17078u}, /* j = 7 */ \
   }
+/* round(cos(j pi/16) * 2^62), j = 1..7 */
+#define FDS_COS_Q62_INIT \
+  {4523073764714963030ll, 4260642322793532497ll, 3834476785802888710ll, 3260954456333195553ll, 2562115475870945497ll, 1764815834521887442ll, 899695310372275547ll}

@@ -1,9 +1,10 @@
 // Device building blocks of the selective-protection kernels (sm_103a).
 //
 //  * 8-point DCT-II / inverse butterflies in float32 (Sect. 6.4.2: separable 8x8 transform)
-//  * AES-128 with one T-table in shared memory and CTR counter blocks (FIPS-197; Sect. 6.12)
+//  * AES-128 with T-tables in shared memory and CTR counter blocks (FIPS-197; Sect. 6.12)
 //  * the exact-rounding fallback (Sect. 6.4.3 reading: round half away from zero of the exact
-//    value): a 64-bit fixed-point re-evaluation, then exact arithmetic in Z[cos(pi/16)]
+//    value): exact integer coordinates in Z[cos(pi/16)], a 128-bit fixed-point decision and,
+//    at a rounding boundary, a 256-bit one that is exact by a norm bound
 #pragma once
 
 #include <stdint.h>
@@ -52,15 +53,13 @@ __host__ __device__ constexpr int zigzag_of(int u, int v) {
 // inputs are exact, which keeps F[0][0], F[0][4], F[4][0], F[4][4] exact (each is an
 // integer / 8).
 template <bool RAT_UNSCALED, bool IRR_LAMBDA>
-__device__ __forceinline__ void dct8(float (&x)[8]) {
+__device__ __forceinline__ void dct8_sd(const float (&s)[4], const float (&d)[4], float (&x)[8]) {
   constexpr double m = IRR_LAMBDA ? kLambda : 1.0;
   constexpr float a2 = (float)(0.5 * m * kC2), a6 = (float)(0.5 * m * kC6);
   constexpr float h1 = (float)(0.5 * m * kC1), h3 = (float)(0.5 * m * kC3);
   constexpr float h5 = (float)(0.5 * m * kC5), h7 = (float)(0.5 * m * kC7);
   constexpr float lam = (float)kLambda;
-  const float s0 = x[0] + x[7], s1 = x[1] + x[6], s2 = x[2] + x[5], s3 = x[3] + x[4];
-  const float d0 = x[0] - x[7], d1 = x[1] - x[6], d2 = x[2] - x[5], d3 = x[3] - x[4];
-  const float e0 = s0 + s3, e1 = s1 + s2, f0 = s0 - s3, f1 = s1 - s2;
+  const float e0 = s[0] + s[3], e1 = s[1] + s[2], f0 = s[0] - s[3], f1 = s[1] - s[2];
   if (RAT_UNSCALED) {
     x[0] = e0 + e1;
     x[4] = e0 - e1;
@@ -71,10 +70,27 @@ __device__ __forceinline__ void dct8(float (&x)[8]) {
   x[2] = fmaf(f0, a2, f1 * a6);
   x[6] = fmaf(f0, a6, f1 * -a2);
   // odd rows of the basis on d_n = x_n - x_(7-n), n = 0..3
-  x[1] = fmaf(d3, h7, fmaf(d2, h5, fmaf(d1, h3, d0 * h1)));
-  x[3] = fmaf(d3, -h5, fmaf(d2, -h1, fmaf(d1, -h7, d0 * h3)));
-  x[5] = fmaf(d3, h3, fmaf(d2, h7, fmaf(d1, -h1, d0 * h5)));
-  x[7] = fmaf(d3, -h1, fmaf(d2, h3, fmaf(d1, -h5, d0 * h7)));
+  x[1] = fmaf(d[3], h7, fmaf(d[2], h5, fmaf(d[1], h3, d[0] * h1)));
+  x[3] = fmaf(d[3], -h5, fmaf(d[2], -h1, fmaf(d[1], -h7, d[0] * h3)));
+  x[5] = fmaf(d[3], h3, fmaf(d[2], h7, fmaf(d[1], -h1, d[0] * h5)));
+  x[7] = fmaf(d[3], -h1, fmaf(d[2], h3, fmaf(d[1], -h5, d[0] * h7)));
+}
+
+template <bool RAT_UNSCALED, bool IRR_LAMBDA>
+__device__ __forceinline__ void dct8(float (&x)[8]) {
+  const float s[4] = {x[0] + x[7], x[1] + x[6], x[2] + x[5], x[3] + x[4]};
+  const float d[4] = {x[0] - x[7], x[1] - x[6], x[2] - x[5], x[3] - x[4]};
+  dct8_sd<RAT_UNSCALED, IRR_LAMBDA>(s, d, x);
+}
+
+// Row pass straight from pixel bytes.  X_i = 2^23 + p_i (a float built from the byte), so
+// d_i = X_i - X_(7-i) = p_i - p_(7-i) and s_i = (X_i - (2^24 + 256)) + X_(7-i) =
+// (p_i - 128) + (p_(7-i) - 128) are exact: the level shift by 128 costs nothing.
+__device__ __forceinline__ void dct8_row_bytes(const float (&X)[8], float (&x)[8]) {
+  constexpr float c2 = 16777472.0f;  // 2^24 + 256
+  const float s[4] = {(X[0] - c2) + X[7], (X[1] - c2) + X[6], (X[2] - c2) + X[5], (X[3] - c2) + X[4]};
+  const float d[4] = {X[0] - X[7], X[1] - X[6], X[2] - X[5], X[3] - X[4]};
+  dct8_sd<true, false>(s, d, x);
 }
 
 // Inverse: X (orthonormal coefficients) -> x_n = sum_k b_k(n) X_k.
@@ -138,48 +154,38 @@ __host__ __device__ inline uint32_t aes_t0(uint8_t x) {
   return (uint32_t)s2 | ((uint32_t)s << 8) | ((uint32_t)s << 16) | ((uint32_t)s3 << 24);
 }
 
-__device__ __forceinline__ uint32_t rotl32(uint32_t x, int n) { return __funnelshift_l(x, x, n); }
-
-// S[x] moved to byte position `pos` of a word; T0[x] holds S[x] in byte 1.
-template <int POS>
-__device__ __forceinline__ uint32_t sbox_at(const uint32_t* T0, uint32_t idx) {
-  uint32_t t = T0[idx];
-  // __byte_perm(t, 0, sel): result byte POS = t byte 1, others = 0 (selector 4 = zero byte)
-  constexpr uint32_t sel = (POS == 0) ? 0x4441u : (POS == 1) ? 0x4414u : (POS == 2) ? 0x4144u : 0x1444u;
-  return __byte_perm(t, 0u, sel);
-}
-
-// Encrypt one block in place.  rk: 44 round-key words; T0: shared-memory table.
+// Encrypt one block in place.  rk: 44 round-key words; T: four shared-memory tables,
+// T[r][x] = rotl(T0[x], 8r) (the MixColumns column of S[x] entering from row r).  The last
+// round takes S[x] from byte 1 of T[0][x].
 __device__ __forceinline__ void aes128_encrypt(uint32_t (&s)[4], const uint32_t* rk,
-                                               const uint32_t* T0) {
+                                               const uint32_t* T) {
+  const uint32_t* T0 = T;
+  const uint32_t* T1 = T + 256;
+  const uint32_t* T2 = T + 512;
+  const uint32_t* T3 = T + 768;
   uint32_t s0 = s[0] ^ rk[0], s1 = s[1] ^ rk[1], s2 = s[2] ^ rk[2], s3 = s[3] ^ rk[3];
 #pragma unroll
   for (int r = 1; r < 10; ++r) {
-    const uint32_t t0 = T0[s0 & 0xff] ^ rotl32(T0[(s1 >> 8) & 0xff], 8) ^
-                        rotl32(T0[(s2 >> 16) & 0xff], 16) ^ rotl32(T0[s3 >> 24], 24) ^ rk[4 * r];
-    const uint32_t t1 = T0[s1 & 0xff] ^ rotl32(T0[(s2 >> 8) & 0xff], 8) ^
-                        rotl32(T0[(s3 >> 16) & 0xff], 16) ^ rotl32(T0[s0 >> 24], 24) ^ rk[4 * r + 1];
-    const uint32_t t2 = T0[s2 & 0xff] ^ rotl32(T0[(s3 >> 8) & 0xff], 8) ^
-                        rotl32(T0[(s0 >> 16) & 0xff], 16) ^ rotl32(T0[s1 >> 24], 24) ^ rk[4 * r + 2];
-    const uint32_t t3 = T0[s3 & 0xff] ^ rotl32(T0[(s0 >> 8) & 0xff], 8) ^
-                        rotl32(T0[(s1 >> 16) & 0xff], 16) ^ rotl32(T0[s2 >> 24], 24) ^ rk[4 * r + 3];
+    const uint32_t t0 = T0[s0 & 0xff] ^ T1[(s1 >> 8) & 0xff] ^ T2[(s2 >> 16) & 0xff] ^ T3[s3 >> 24] ^ rk[4 * r];
+    const uint32_t t1 = T0[s1 & 0xff] ^ T1[(s2 >> 8) & 0xff] ^ T2[(s3 >> 16) & 0xff] ^ T3[s0 >> 24] ^ rk[4 * r + 1];
+    const uint32_t t2 = T0[s2 & 0xff] ^ T1[(s3 >> 8) & 0xff] ^ T2[(s0 >> 16) & 0xff] ^ T3[s1 >> 24] ^ rk[4 * r + 2];
+    const uint32_t t3 = T0[s3 & 0xff] ^ T1[(s0 >> 8) & 0xff] ^ T2[(s1 >> 16) & 0xff] ^ T3[s2 >> 24] ^ rk[4 * r + 3];
     s0 = t0;
     s1 = t1;
     s2 = t2;
     s3 = t3;
   }
-  s[0] = sbox_at<0>(T0, s0 & 0xff) | sbox_at<1>(T0, (s1 >> 8) & 0xff) |
-         sbox_at<2>(T0, (s2 >> 16) & 0xff) | sbox_at<3>(T0, s3 >> 24);
-  s[1] = sbox_at<0>(T0, s1 & 0xff) | sbox_at<1>(T0, (s2 >> 8) & 0xff) |
-         sbox_at<2>(T0, (s3 >> 16) & 0xff) | sbox_at<3>(T0, s0 >> 24);
-  s[2] = sbox_at<0>(T0, s2 & 0xff) | sbox_at<1>(T0, (s3 >> 8) & 0xff) |
-         sbox_at<2>(T0, (s0 >> 16) & 0xff) | sbox_at<3>(T0, s1 >> 24);
-  s[3] = sbox_at<0>(T0, s3 & 0xff) | sbox_at<1>(T0, (s0 >> 8) & 0xff) |
-         sbox_at<2>(T0, (s1 >> 16) & 0xff) | sbox_at<3>(T0, s2 >> 24);
-  s[0] ^= rk[40];
-  s[1] ^= rk[41];
-  s[2] ^= rk[42];
-  s[3] ^= rk[43];
+  // last round: SubBytes + ShiftRows + AddRoundKey; byte r of column c = S[row r of column c+r]
+  // (__byte_perm selector 0x4441 etc. moves byte 1 of T0[x] to byte r, zeroing the rest)
+  auto sb = [&](uint32_t idx, uint32_t sel) { return __byte_perm(T0[idx], 0u, sel); };
+  s[0] = (sb(s0 & 0xff, 0x4441u) | sb((s1 >> 8) & 0xff, 0x4414u) | sb((s2 >> 16) & 0xff, 0x4144u) |
+          sb(s3 >> 24, 0x1444u)) ^ rk[40];
+  s[1] = (sb(s1 & 0xff, 0x4441u) | sb((s2 >> 8) & 0xff, 0x4414u) | sb((s3 >> 16) & 0xff, 0x4144u) |
+          sb(s0 >> 24, 0x1444u)) ^ rk[41];
+  s[2] = (sb(s2 & 0xff, 0x4441u) | sb((s3 >> 8) & 0xff, 0x4414u) | sb((s0 >> 16) & 0xff, 0x4144u) |
+          sb(s1 >> 24, 0x1444u)) ^ rk[42];
+  s[3] = (sb(s3 & 0xff, 0x4441u) | sb((s0 >> 8) & 0xff, 0x4414u) | sb((s1 >> 16) & 0xff, 0x4144u) |
+          sb(s2 >> 24, 0x1444u)) ^ rk[43];
 }
 
 // Counter block IV + n (128-bit big-endian addition) as four state columns.
@@ -261,6 +267,50 @@ __device__ inline int exact_sign(int a0, const int (&n)[9], bool* fail) {
   }
   *fail = true;
   return 1;
+}
+
+// round(c(j) 2^62), j = 1..7
+static __constant__ long long c_cos_q62[7] = FDS_COS_Q62_INIT;
+
+// Round half away from zero, exactly, of the value V with 8V = n[0] + sum_{j=1..7} n[j] c(j).
+// First in 64-bit fixed point (error <= sum|n[j]| units of 2^-62 of 8V), which decides unless
+// 8V is that close to an odd multiple of 4 (a rounding boundary); then exact_sign decides.
+// *escalated counts the exact_sign calls with a nonzero irrational part.
+__device__ inline int exact_round(const int (&n)[9], int* escalated, bool* fail) {
+  __int128 d = (__int128)n[0] << 62;
+  long long err = 0;
+#pragma unroll
+  for (int j = 1; j < 8; ++j) {
+    d += (__int128)n[j] * (__int128)c_cos_q62[j - 1];
+    err += n[j] < 0 ? -(long long)n[j] : (long long)n[j];
+  }
+  // X / 2^65 = V + 1/2; floor of it is the answer away from the boundaries
+  const __int128 X = d + ((__int128)4 << 62);
+  const long long q = (long long)(X >> 65);
+  const __int128 rem = X - ((__int128)q << 65);                 // in [0, 2^65)
+  if (rem > (__int128)err && rem < ((__int128)1 << 65) - (__int128)err) return (int)q;
+  const int upper = rem <= (__int128)err ? (int)q : (int)q + 1;  // boundary at V = upper - 1/2
+  if (err) ++*escalated;
+  const int sgn = exact_sign(n[0] - 8 * upper + 4, n, fail);
+  return sgn > 0 ? upper : (sgn < 0 ? upper - 1 : (upper >= 1 ? upper : upper - 1));
+}
+
+// d = c + sum of the four products of unsigned bytes of a with signed bytes of b
+__device__ __forceinline__ int dp4a_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// d = c + a.lo16 * b.byte0 + a.hi16 * b.byte1 (lo) or ... b.byte2, b.byte3 (hi), all signed
+__device__ __forceinline__ int dp2a_lo(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.lo.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.hi.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
 }
 
 }  // namespace fds

@@ -1,236 +1,254 @@
 // Fused protect kernel (Sect. 6.3.1, Fig. 6): 8x8 DCT-II per channel, int16 rounding,
-// zigzag fragmentation, AES-128-CTR of the confidential fragment.  Per tile:
-//   1. cp.async the pixels (8 rows x 24 bytes per block) into shared memory
-//   2. per channel-block: row then column float32 butterflies, round every coefficient to
-//      int16, write it to the public or private staging area at its zigzag position;
-//      coefficients within the float32 error guard of a half-integer go to a queue
-//   3. the queue is resolved exactly (64-bit fixed point; exact arithmetic in Z[cos(pi/16)]
-//      when that is still ambiguous)
-//   4. AES-128-CTR over the private staging area, one thread per 16-byte keystream block
-//   5. coalesced 16-byte stores of both staging areas
+// zigzag fragmentation, AES-128-CTR of the confidential fragment.
+//
+// Persistent CTAs; per tile (see fds_tile.cuh for the decomposition):
+//   A. the tile's pixels (prefetched with cp.async during the previous tile) are in shared
+//      memory; the previous tile's fragments leave through bulk (TMA engine) stores and the
+//      next tile's pixels start loading
+//   1. per channel-block: row then column float32 butterflies; every coefficient rounded to
+//      int16 and written to the public or private staging area at its zigzag position;
+//      coefficients within the float32 error guard of a half-integer are queued
+//   B. 2. queued coefficients are re-decided exactly (integer coordinates in Z[cos(pi/16)])
+//   C. 3. AES-128-CTR over the private staging area, one thread per 16-byte keystream block
+// Staging is double-buffered so a tile's stores overlap the next tile's transform.
 #include "fds_tile.cuh"
 
 namespace fds {
 
-// Exact rounding of coefficient `pos` = 8u+v of channel c of tile block b.
-__device__ __noinline__ int resolve_fwd(const uint8_t* tile, int b, int c, int pos, float v,
-                                        const int32_t* bfwd, int* n3, bool* fail) {
-  const int m = (int)floorf(v);
-  const uint8_t* px = tile + b * 24 + c;
-  // stage 2: 64-bit fixed point; |acc - 8F 2^28| <= (1/2 + tiny) sum p
-  long long acc = 0, err = 0;
-  const int32_t* row = bfwd + pos * 64;
-  for (int y = 0; y < 8; ++y) {
-#pragma unroll
-    for (int x = 0; x < 8; ++x) {
-      const int p = px[y * kRowBytes + 3 * x];
-      acc += (long long)p * row[8 * y + x];
-      err += p;
-    }
-  }
-  const long long d = acc - ((long long)(8 * m + 4) << kFixShift);
-  if (d > err + 1) return m + 1;
-  if (d < -err - 1) return m;
-  // stage 3: exact coordinates in Z[cos(pi/16)]
-  ++*n3;
-  const int u = pos >> 3, vv = pos & 7;
-  int n[9];
-#pragma unroll
-  for (int j = 0; j < 9; ++j) n[j] = 0;
-  for (int y = 0; y < 8; ++y) {
-    const int al = u == 0 ? 4 : (2 * y + 1) * u;
-    for (int x = 0; x < 8; ++x) {
-      const int be = vv == 0 ? 4 : (2 * x + 1) * vv;
-      const int p = px[y * kRowBytes + 3 * x];
-      add_cos_term(n, al - be, p);
-      add_cos_term(n, al + be, p);
-    }
-  }
-  return pick(m, exact_sign(n[0] - 8 * m - 4, n, fail));
-}
+constexpr int kSmemPix = 0;                                  // 2 pixel tiles
+constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 2 staging areas
+constexpr int kSmemT = kSmemStage + 2 * kCoefBytes;          // AES tables, 4 KB
+constexpr int kSmemQueue = kSmemT + 4096;                    // near-tie queue
+constexpr int kSmemBlk = kSmemQueue + 4 * kQueueCap;         // 2 x 64 block offsets
+constexpr int kSmemMisc = kSmemBlk + 2 * 8 * kTileBlocks;
+constexpr int kSmemBytes = kSmemMisc + 32;
 
 template <int K, bool DEBUG>
-__global__ void __launch_bounds__(kThreads) protect_kernel(const __grid_constant__ TileArgs a) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint8_t* tile = smem + kSmemPix;
-  uint8_t* coef = smem + kSmemCoef;
-  const uint32_t* T0s = reinterpret_cast<const uint32_t*>(smem + kSmemT0);
-  QEntry* queue = reinterpret_cast<QEntry*>(smem + kSmemQueue);
-  const uint64_t* blk = reinterpret_cast<const uint64_t*>(smem + kSmemBlk);
-  int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
-
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
+  uint64_t* blk = reinterpret_cast<uint64_t*>(smem + kSmemBlk);
+  int* misc = reinterpret_cast<int*>(smem + kSmemMisc);  // [0] queue size [1] queued total
+                                                          // [2] escalations [3] failures
   const int k = K >= 0 ? K : a.k;
   const int npub = 63 - k;
   const int t = threadIdx.x;
-  const int b0 = blockIdx.x * kTileBlocks;
-  const int nb = min(kTileBlocks, a.nblocks - b0);
+  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
   const uint64_t w3 = (uint64_t)a.width * 3ull;
+  int tile = blockIdx.x;
+  if (tile >= ntiles) return;
 
-  tile_prologue(a, smem, b0, nb);
-  __syncthreads();
-  for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
-    const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
-    const int b = rem / 3, q = rem - 3 * b;
-    if (b < nb) cp_async8(tile + y * kRowBytes + b * 24 + 8 * q, a.pixels_in + blk[b] + y * w3 + 8 * q);
-  }
-  cp_async_wait_all();
+  for (int i = t; i < 1024; i += kThreads) Ts[i] = a.T[i];
+  if (t < 8) misc[t] = 0;
+  if (t < kTileBlocks && tile * kTileBlocks + t < a.nblocks) blk[t] = block_offset(a, tile * kTileBlocks + t);
   __syncthreads();
 
-  int16_t* pubst = reinterpret_cast<int16_t*>(coef);
-  int16_t* privst = reinterpret_cast<int16_t*>(coef + kTileCb * 2 * npub);
-  int n3 = 0;
-  bool fail = false;
-  const int cb = t, b = t / 3, c = t - 3 * (t / 3);
+  auto issue_pixels = [&](int tl, int buf) {
+    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
+    uint8_t* pix = smem + kSmemPix + buf * kPixBytes;
+    const uint64_t* bo = blk + buf * kTileBlocks;
+    for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
+      const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
+      const int b = rem / 3, q = rem - 3 * b;
+      if (b < nbl) cp_async8(pix + y * kRowBytes + b * 24 + 8 * q, a.pixels_in + bo[b] + y * w3 + 8 * q);
+    }
+    cp_async_commit();
+  };
+  // the fragments of tile tl, staged in buffer buf, to global memory (one thread)
+  auto issue_store = [&](int tl, int buf) {
+    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
+    const uint8_t* st = smem + kSmemStage + buf * kCoefBytes;
+    const int pub_bytes = nbl * 6 * npub, priv_bytes = nbl * 6 * (k + 1);
+    uint8_t* pdst = reinterpret_cast<uint8_t*>(a.pub_out) + (uint64_t)tl * kTileBlocks * 6ull * npub;
+    uint8_t* vdst = a.priv_out + (uint64_t)tl * kTileBlocks * 6ull * (k + 1);
+    const uint8_t* vsrc = st + kTileCb * 2 * npub;
+    if (pub_bytes >> 4) bulk_store(pdst, st, (uint32_t)(pub_bytes & ~15));
+    if (priv_bytes >> 4) bulk_store(vdst, vsrc, (uint32_t)(priv_bytes & ~15));
+    bulk_commit();
+    for (int j = pub_bytes & ~15; j < pub_bytes; j += 2)
+      *reinterpret_cast<uint16_t*>(pdst + j) = *reinterpret_cast<const uint16_t*>(st + j);
+    for (int j = priv_bytes & ~15; j < priv_bytes; j += 2)
+      *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
+  };
 
-  if (b < nb) {
-    float f[8][8];
-    // rows: channel c's bytes of the block row, level-shifted by 128 (exact)
-#pragma unroll
-    for (int y = 0; y < 8; ++y) {
-      uint32_t w[6];
-      load_row_shifted(tile, y, b, c, w);
-#pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const int byte = 3 * x;
-        f[y][x] = __int_as_float(__byte_perm(w[byte >> 2], 0x4B000000u, 0x7440u | (byte & 3))) -
-                  8388736.0f;
-      }
-      dct8<true, false>(f[y]);
+  issue_pixels(tile, 0);
+  int it = 0, prev = -1;
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    const int buf = it & 1;
+    const int next = tile + gridDim.x;
+    const int nb = min(kTileBlocks, a.nblocks - tile * kTileBlocks);
+    if (next < ntiles && t < kTileBlocks && next * kTileBlocks + t < a.nblocks)
+      blk[(buf ^ 1) * kTileBlocks + t] = block_offset(a, next * kTileBlocks + t);
+    cp_async_wait_all();
+    if (t == 0) {
+      if (!DEBUG) bulk_wait_read_all();   // staging[buf] is no longer read by older stores
+      misc[0] = 0;
     }
-    // columns; columns 0 and 4 hold unscaled (exact integer) row outputs
+    __syncthreads();                                                       // A
+    if (!DEBUG && t == 0 && prev >= 0) issue_store(prev, buf ^ 1);
+    if (next < ntiles) issue_pixels(next, buf ^ 1);
+
+    const uint8_t* tile_px = smem + kSmemPix + buf * kPixBytes;
+    int16_t* pubst = reinterpret_cast<int16_t*>(smem + kSmemStage + buf * kCoefBytes);
+    int16_t* privst = reinterpret_cast<int16_t*>(smem + kSmemStage + buf * kCoefBytes + kTileCb * 2 * npub);
+    const int cb = t, b = t / 3, c = t - 3 * (t / 3);
+    if (b < nb) {
+      float f[8][8];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      float col[8];
+      for (int y = 0; y < 8; ++y) {
+        uint32_t w[6];
+        load_row_shifted(tile_px, y, b, c, w);
+        float X[8];
 #pragma unroll
-      for (int y = 0; y < 8; ++y) col[y] = f[y][v];
-      if (v == 0 || v == 4)
-        dct8<true, true>(col);
-      else
-        dct8<false, false>(col);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) f[u][v] = col[u];
-    }
-    if (DEBUG) {
-      float* out = a.dbg_coefs + ((uint64_t)b0 * 3 + cb) * 64;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          float val = f[u][v];
-          if (u == 0 && v == 0)
-            val = (val + 8192.0f) * 0.125f;
-          else if ((u == 0 || u == 4) && (v == 0 || v == 4))
-            val *= 0.125f;
-          out[8 * u + v] = val;
+        for (int x = 0; x < 8; ++x) {
+          const int byte = 3 * x;
+          X[x] = __int_as_float(__byte_perm(w[byte >> 2], 0x4B000000u, 0x7440u | (byte & 3)));
         }
-    } else {
-      // rounding: the four rational positions exactly in integers, the rest to nearest in
-      // float32 with the residual checked against the guard
-      int16_t* pub_cb = pubst + cb * npub;
-      int16_t* priv_cb = privst + cb * (k + 1);
-      float maxr = 0.0f;
+        dct8_row_bytes(X, f[y]);
+      }
+      // columns; columns 0 and 4 hold unscaled (exact integer) row outputs
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int v = 0; v < 8; ++v) {
+        float col[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int z = zigzag_of(u, v);
-          int q;
-          if ((u == 0 || u == 4) && (v == 0 || v == 4)) {
-            const int T = __float_as_int(f[u][v] + kMagic) - kMagicBits;  // 8 F, exact
-            q = (u == 0 && v == 0) ? ((T + 4) >> 3) + 1024 : (T + 4 - (T < 0 ? 1 : 0)) >> 3;
-          } else {
-            const float yv = f[u][v] + kMagic;
-            q = __float_as_int(yv) - kMagicBits;
-            maxr = fmaxf(maxr, fabsf(f[u][v] - (yv - kMagic)));
+        for (int y = 0; y < 8; ++y) col[y] = f[y][v];
+        if (v == 0 || v == 4)
+          dct8<true, true>(col);
+        else
+          dct8<false, false>(col);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) f[u][v] = col[u];
+      }
+      if (DEBUG) {
+        float* out = a.dbg_coefs + ((uint64_t)tile * kTileBlocks * 3 + cb) * 64;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            float val = f[u][v];
+            if (u == 0 && v == 0)
+              val = (val + 8192.0f) * 0.125f;
+            else if ((u == 0 || u == 4) && (v == 0 || v == 4))
+              val *= 0.125f;
+            out[8 * u + v] = val;
           }
-          if (z <= k)
-            priv_cb[z] = (int16_t)q;
-          else
-            pub_cb[z - k - 1] = (int16_t)q;
-        }
-      }
-      if (maxr > 0.5f - kGuardFwd) {
+      } else {
+        // rounding: the four rational positions exactly in integers; the rest to nearest in
+        // float32, residual checked against the guard (near ties marked in a 64-bit mask)
+        int16_t* pub_cb = pubst + cb * npub;
+        int16_t* priv_cb = privst + cb * (k + 1);
+        uint32_t mlo = 0, mhi = 0;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
-            if ((u == 0 || u == 4) && (v == 0 || v == 4)) continue;
-            const float yv = f[u][v] + kMagic;
-            if (fabsf(f[u][v] - (yv - kMagic)) > 0.5f - kGuardFwd) {
-              const int idx = atomicAdd(&misc[0], 1);
-              if (idx < kQueueCap) {
-                queue[idx] = QEntry{(uint16_t)cb, (uint8_t)(8 * u + v), 0, f[u][v]};
-              } else {  // queue full: resolve here
-                const int q = resolve_fwd(tile, b, c, 8 * u + v, f[u][v], a.bfwd, &n3, &fail);
-                const int z = zigzag_of(u, v);
-                if (z <= k)
-                  priv_cb[z] = (int16_t)q;
+            const int z = zigzag_of(u, v);
+            uint32_t q;
+            if ((u == 0 || u == 4) && (v == 0 || v == 4)) {
+              const int T = __float_as_int(f[u][v] + kMagic) - kMagicBits;  // 8 F, exact
+              q = (uint32_t)((u == 0 && v == 0) ? ((T + 4) >> 3) + 1024 : (T + 4 - (T < 0 ? 1 : 0)) >> 3);
+            } else {
+              const float yv = f[u][v] + kMagic;
+              q = __float_as_uint(yv);                 // low 16 bits: the int16 result
+              if (fabsf(f[u][v] - (yv - kMagic)) > 0.5f - kGuardFwd) {
+                if (8 * u + v < 32)
+                  mlo |= 1u << (8 * u + v);
                 else
-                  pub_cb[z - k - 1] = (int16_t)q;
+                  mhi |= 1u << (8 * u + v - 32);
               }
             }
+            if (z <= k)
+              priv_cb[z] = (int16_t)q;
+            else
+              pub_cb[z - k - 1] = (int16_t)q;
+          }
+        }
+        uint64_t mask = ((uint64_t)mhi << 32) | mlo;
+        while (mask) {
+          const int pos = __ffsll((long long)mask) - 1;
+          mask &= mask - 1;
+          const int idx = atomicAdd(&misc[0], 1);
+          if (idx < kQueueCap) {
+            queue[idx] = ((uint32_t)cb << 8) | (uint32_t)pos;
+          } else {  // queue full: decide here
+            int n[9], esc = 0;
+            bool fail = false;
+            coords_fwd(tile_px, b, c, pos, a.cfwd, n);
+            const int q = exact_round(n, &esc, &fail);
+            const int z = zigzag_of(pos >> 3, pos & 7);
+            if (z <= k)
+              priv_cb[z] = (int16_t)q;
+            else
+              pub_cb[z - k - 1] = (int16_t)q;
+            if (esc) atomicAdd(&misc[2], esc);
+            if (fail) atomicAdd(&misc[3], 1);
           }
         }
       }
     }
+    if (DEBUG) continue;
+    __syncthreads();                                                       // B
+    {
+      const int nq = min(misc[0], kQueueCap);
+      int esc = 0;
+      bool fail = false;
+      for (int i = t; i < nq; i += kThreads) {
+        const uint32_t e = queue[i];
+        const int ecb = (int)(e >> 8), pos = (int)(e & 255);
+        const int eb = ecb / 3, ec = ecb - 3 * eb;
+        int n[9];
+        coords_fwd(tile_px, eb, ec, pos, a.cfwd, n);
+        const int q = exact_round(n, &esc, &fail);
+        const int z = zigzag_of(pos >> 3, pos & 7);
+        if (z <= k)
+          privst[ecb * (k + 1) + z] = (int16_t)q;
+        else
+          pubst[ecb * npub + z - k - 1] = (int16_t)q;
+      }
+      if (esc) atomicAdd(&misc[2], esc);
+      if (fail) atomicAdd(&misc[3], 1);
+      if (t == 0) misc[1] += misc[0];
+    }
+    __syncthreads();                                                       // C
+    ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
+             ((uint64_t)tile * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, a, Ts);
+    fence_proxy_async();
+    prev = tile;
   }
   if (DEBUG) return;
   __syncthreads();
-  const int nq = min(misc[0], kQueueCap);
-  for (int i = t; i < nq; i += kThreads) {
-    const QEntry e = queue[i];
-    const int eb = e.cb / 3, ec = e.cb - 3 * eb;
-    const int q = resolve_fwd(tile, eb, ec, e.pos, e.v, a.bfwd, &n3, &fail);
-    const int z = zigzag_of(e.pos >> 3, e.pos & 7);
-    if (z <= k)
-      privst[e.cb * (k + 1) + z] = (int16_t)q;
-    else
-      pubst[e.cb * npub + z - k - 1] = (int16_t)q;
+  if (t == 0) {
+    if (prev >= 0) issue_store(prev, (it - 1) & 1);
+    bulk_wait_all();
+    if (a.counters) {
+      if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
+      if (misc[2]) atomicAdd(&a.counters[1], (unsigned long long)misc[2]);
+      if (misc[3]) atomicAdd(&a.counters[2], (unsigned long long)misc[3]);
+    }
   }
-  if (n3) atomicAdd(&misc[1], n3);
-  if (fail) atomicAdd(&misc[2], 1);
-  __syncthreads();
-
-  // AES-128-CTR over the private staging area
-  const int priv_bytes = nb * 6 * (k + 1);
-  const uint64_t priv_off = (uint64_t)b0 * 6ull * (uint64_t)(k + 1);  // multiple of 16
-  ctr_tile(reinterpret_cast<uint8_t*>(privst), priv_bytes, priv_off >> 4, a, T0s);
-  __syncthreads();
-
-  // coalesced stores
-  {
-    const int bytes = nb * 6 * npub;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(a.pub_out) + (uint64_t)b0 * 6ull * (uint64_t)npub;
-    const uint8_t* src = reinterpret_cast<const uint8_t*>(pubst);
-    const int n16 = bytes >> 4;
-    for (int i = t; i < n16; i += kThreads)
-      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
-    for (int j = (n16 << 4) + 2 * t; j < bytes; j += 2 * kThreads)
-      *reinterpret_cast<uint16_t*>(dst + j) = *reinterpret_cast<const uint16_t*>(src + j);
-  }
-  {
-    uint8_t* dst = a.priv_out + priv_off;
-    const uint8_t* src = reinterpret_cast<const uint8_t*>(privst);
-    const int n16 = priv_bytes >> 4;
-    for (int i = t; i < n16; i += kThreads)
-      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
-    for (int j = (n16 << 4) + 2 * t; j < priv_bytes; j += 2 * kThreads)
-      *reinterpret_cast<uint16_t*>(dst + j) = *reinterpret_cast<const uint16_t*>(src + j);
-  }
-  tile_epilogue_counters(a, smem);
 }
 
-cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug) {
-  const int grid = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
-  if (debug)
-    protect_kernel<-1, true><<<grid, kThreads, kSmemBytes, s>>>(a);
-  else if (a.k == 0)
-    protect_kernel<0, false><<<grid, kThreads, kSmemBytes, s>>>(a);
-  else if (a.k == 5)
-    protect_kernel<5, false><<<grid, kThreads, kSmemBytes, s>>>(a);
-  else
-    protect_kernel<-1, false><<<grid, kThreads, kSmemBytes, s>>>(a);
+template <int K, bool DEBUG>
+static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(protect_kernel<K, DEBUG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
+  const int grid = ntiles < kCtasPerSm * sms ? ntiles : kCtasPerSm * sms;
+  protect_kernel<K, DEBUG><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms) {
+  if (debug) return launch_k<-1, true>(a, s, sms);
+  if (a.k == 0) return launch_k<0, false>(a, s, sms);
+  if (a.k == 5) return launch_k<5, false>(a, s, sms);
+  return launch_k<-1, false>(a, s, sms);
 }
 
 }  // namespace fds

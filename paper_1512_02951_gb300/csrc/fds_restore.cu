@@ -1,138 +1,132 @@
 // Fused restore kernel (defragmentation, Sect. 3.2, Fig. 3; inverse of Sect. 6.3.1): CTR
 // decryption of the confidential fragment, merge with the public fragment by zigzag
-// position, inverse 8x8 DCT, round half away from zero (exact), clamp to [0, 255].  Per tile:
-//   1. cp.async the public and private fragment ranges of the tile into shared memory
-//   2. AES-128-CTR decryption of the private range in place
-//   3. per channel-block: column then row float32 inverse butterflies, round + clamp, write
-//      the bytes into the interleaved pixel tile; values within the float32 error guard of a
-//      half-integer go to a queue, resolved exactly afterwards
-//   4. coalesced 8-byte stores of the pixel tile
+// position, inverse 8x8 DCT, round half away from zero (exact), clamp to [0, 255].
+//
+// Persistent CTAs; per tile (see fds_tile.cuh for the decomposition):
+//   A. the tile's fragment ranges (prefetched with cp.async during the previous tile) are in
+//      shared memory; the next tile's start loading
+//   1. AES-128-CTR decryption of the private range in place
+//   B. 2. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
+//      into the interleaved pixel tile; values within the float32 error guard of a
+//      half-integer are queued
+//   C. 3. queued pixels are re-decided exactly (integer coordinates in Z[cos(pi/16)])
+//   D. 4. the pixel tile goes to global memory with 8-byte stores
 #include "fds_tile.cuh"
 
 namespace fds {
 
-// Exact rounding of pixel `pos` = 8y+x of tile channel-block cb from its int16 coefficients.
-__device__ __noinline__ int resolve_inv(const int16_t* pubst, const int16_t* privst, int cb,
-                                        int pos, float v, int k, const int32_t* binv, int* n3,
-                                        bool* fail) {
-  const int m = (int)floorf(v);
-  // stage 2: 64-bit fixed point; |acc - 8p 2^28| <= (1/2 + tiny) sum |F|
-  long long acc = 0, err = 0;
-  const int32_t* row = binv + pos * 64;
-  for (int z = 0; z < 64; ++z) {
-    const int q = coef_at(pubst, privst, cb, z, k);
-    acc += (long long)q * row[z];
-    err += q < 0 ? -q : q;
-  }
-  const long long d = acc - ((long long)(8 * m + 4) << kFixShift);
-  if (d > err + 1) return m + 1;
-  if (d < -err - 1) return m;
-  // stage 3: exact coordinates in Z[cos(pi/16)]
-  ++*n3;
-  const int y = pos >> 3, x = pos & 7;
-  int n[9];
+constexpr int kSmemCoef = 0;                                 // 2 fragment staging areas
+constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 1 pixel tile
+constexpr int kSmemT = kSmemPix + kPixBytes;                 // AES tables, 4 KB
+constexpr int kSmemQueue = kSmemT + 4096;
+constexpr int kSmemBlk = kSmemQueue + 4 * kQueueCap;
+constexpr int kSmemMisc = kSmemBlk + 8 * kTileBlocks;
+constexpr int kSmemBytes = kSmemMisc + 32;
+
+// gather the 64 int16 coefficients of tile channel-block cb in zigzag order, two per word
+__device__ __forceinline__ void gather_coefs(const int16_t* pubst, const int16_t* privst, int cb,
+                                             int k, uint32_t (&Q)[32]) {
+  const uint16_t* pu = reinterpret_cast<const uint16_t*>(pubst) + cb * (63 - k) - (k + 1);
+  const uint16_t* pv = reinterpret_cast<const uint16_t*>(privst) + cb * (k + 1);
 #pragma unroll
-  for (int j = 0; j < 9; ++j) n[j] = 0;
-  for (int u = 0; u < 8; ++u) {
-    const int al = u == 0 ? 4 : (2 * y + 1) * u;
-    for (int vv = 0; vv < 8; ++vv) {
-      const int be = vv == 0 ? 4 : (2 * x + 1) * vv;
-      const int q = coef_at(pubst, privst, cb, zigzag_of(u, vv), k);
-      add_cos_term(n, al - be, q);
-      add_cos_term(n, al + be, q);
-    }
+  for (int i = 0; i < 32; ++i) {
+    const uint32_t lo = 2 * i <= k ? pv[2 * i] : pu[2 * i];
+    const uint32_t hi = 2 * i + 1 <= k ? pv[2 * i + 1] : pu[2 * i + 1];
+    Q[i] = lo | (hi << 16);
   }
-  return pick(m, exact_sign(n[0] - 8 * m - 4, n, fail));
 }
 
 template <int K>
-__global__ void __launch_bounds__(kThreads) restore_kernel(const __grid_constant__ TileArgs a) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint8_t* tile = smem + kSmemPix;
-  uint8_t* coef = smem + kSmemCoef;
-  const uint32_t* T0s = reinterpret_cast<const uint32_t*>(smem + kSmemT0);
-  QEntry* queue = reinterpret_cast<QEntry*>(smem + kSmemQueue);
-  const uint64_t* blk = reinterpret_cast<const uint64_t*>(smem + kSmemBlk);
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* pix = smem + kSmemPix;
+  uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
+  uint64_t* blk = reinterpret_cast<uint64_t*>(smem + kSmemBlk);
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
 
   const int k = K >= 0 ? K : a.k;
   const int npub = 63 - k;
   const int t = threadIdx.x;
-  const int b0 = blockIdx.x * kTileBlocks;
-  const int nb = min(kTileBlocks, a.nblocks - b0);
+  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
   const uint64_t w3 = (uint64_t)a.width * 3ull;
+  int tile = blockIdx.x;
+  if (tile >= ntiles) return;
 
-  int16_t* pubst = reinterpret_cast<int16_t*>(coef);
-  int16_t* privst = reinterpret_cast<int16_t*>(coef + kTileCb * 2 * npub);
-  const int pub_bytes = nb * 6 * npub;
-  const int priv_bytes = nb * 6 * (k + 1);
-  const uint64_t pub_off = (uint64_t)b0 * 6ull * (uint64_t)npub;
-  const uint64_t priv_off = (uint64_t)b0 * 6ull * (uint64_t)(k + 1);
+  for (int i = t; i < 1024; i += kThreads) Ts[i] = a.T[i];
+  if (t < 8) misc[t] = 0;
 
-  tile_prologue(a, smem, b0, nb);
-  {
-    const uint8_t* src = reinterpret_cast<const uint8_t*>(a.pub_in) + pub_off;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(pubst);
-    const int n16 = pub_bytes >> 4;
-    for (int i = t; i < n16; i += kThreads) cp_async16(dst + 16 * i, src + 16 * i);
-    for (int j = (n16 << 4) + 2 * t; j < pub_bytes; j += 2 * kThreads)
-      *reinterpret_cast<uint16_t*>(dst + j) = *reinterpret_cast<const uint16_t*>(src + j);
-  }
-  {
-    const uint8_t* src = a.priv_in + priv_off;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(privst);
-    const int n16 = priv_bytes >> 4;
-    for (int i = t; i < n16; i += kThreads) cp_async16(dst + 16 * i, src + 16 * i);
-    for (int j = (n16 << 4) + 2 * t; j < priv_bytes; j += 2 * kThreads)
-      *reinterpret_cast<uint16_t*>(dst + j) = *reinterpret_cast<const uint16_t*>(src + j);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  ctr_tile(reinterpret_cast<uint8_t*>(privst), priv_bytes, priv_off >> 4, a, T0s);
-  __syncthreads();
+  // cp.async the tile's public and private ranges into staging buffer buf
+  auto issue_frag = [&](int tl, int buf) {
+    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
+    uint8_t* st = smem + kSmemCoef + buf * kCoefBytes;
+    const int pub_bytes = nbl * 6 * npub, priv_bytes = nbl * 6 * (k + 1);
+    const uint8_t* psrc = reinterpret_cast<const uint8_t*>(a.pub_in) + (uint64_t)tl * kTileBlocks * 6ull * npub;
+    const uint8_t* vsrc = a.priv_in + (uint64_t)tl * kTileBlocks * 6ull * (k + 1);
+    uint8_t* vdst = st + kTileCb * 2 * npub;
+    const int p16 = pub_bytes >> 4, v16 = priv_bytes >> 4;
+    for (int i = t; i < p16 + v16; i += kThreads) {
+      if (i < p16)
+        cp_async16(st + 16 * i, psrc + 16 * i);
+      else
+        cp_async16(vdst + 16 * (i - p16), vsrc + 16 * (i - p16));
+    }
+    for (int j = (p16 << 4) + 2 * t; j < pub_bytes; j += 2 * kThreads)
+      *reinterpret_cast<uint16_t*>(st + j) = *reinterpret_cast<const uint16_t*>(psrc + j);
+    for (int j = (v16 << 4) + 2 * t; j < priv_bytes; j += 2 * kThreads)
+      *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
+    cp_async_commit();
+  };
 
-  int n3 = 0;
+  issue_frag(tile, 0);
+  int it = 0;
+  int esc = 0;
   bool fail = false;
-  const int cb = t, b = t / 3, c = t - 3 * (t / 3);
-  if (b < nb) {
-    const int16_t* pub_cb = pubst + cb * npub;
-    const int16_t* priv_cb = privst + cb * (k + 1);
-    float f[8][8];
-    float l1 = 0.0f;  // sum |F|, exact (integers below 2^24)
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    const int buf = it & 1;
+    const int next = tile + gridDim.x;
+    const int nb = min(kTileBlocks, a.nblocks - tile * kTileBlocks);
+    cp_async_wait_all();
+    if (t == 0) misc[0] = 0;
+    __syncthreads();                                                       // A
+    if (next < ntiles) issue_frag(next, buf ^ 1);
+    if (t < nb) blk[t] = block_offset(a, tile * kTileBlocks + t);
+    uint8_t* st = smem + kSmemCoef + buf * kCoefBytes;
+    const int16_t* pubst = reinterpret_cast<const int16_t*>(st);
+    int16_t* privst = reinterpret_cast<int16_t*>(st + kTileCb * 2 * npub);
+    ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
+             ((uint64_t)tile * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, a, Ts);
+    __syncthreads();                                                       // B
+
+    const int cb = t, b = t / 3, c = t - 3 * (t / 3);
+    if (b < nb) {
+      const int16_t* pub_cb = pubst + cb * npub;
+      const int16_t* priv_cb = privst + cb * (k + 1);
+      float f[8][8];
+      float l1 = 0.0f;  // sum |F|, exact (integers below 2^24)
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const int z = zigzag_of(u, v);
+          const int q = z <= k ? priv_cb[z] : pub_cb[z - k - 1];
+          f[u][v] = __int_as_float(kMagicBits + q) - kMagic;
+          l1 += fabsf(f[u][v]);
+        }
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
-        const int z = zigzag_of(u, v);
-        const int q = z <= k ? priv_cb[z] : pub_cb[z - k - 1];
-        f[u][v] = __int_as_float(kMagicBits + q) - kMagic;
-        l1 += fabsf(f[u][v]);
+        float col[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) col[u] = f[u][v];
+        idct8(col);
+#pragma unroll
+        for (int y = 0; y < 8; ++y) f[y][v] = col[y];
       }
-    // columns (over u), then rows (over v)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      float col[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) col[u] = f[u][v];
-      idct8(col);
-#pragma unroll
-      for (int y = 0; y < 8; ++y) f[y][v] = col[y];
-    }
-#pragma unroll
-    for (int y = 0; y < 8; ++y) idct8(f[y]);
-    const float thr = 0.5f - l1 * kGuardInvScale;
-    uint8_t* out = tile + b * 24 + c;
-    float maxr = 0.0f;
-#pragma unroll
-    for (int y = 0; y < 8; ++y)
-#pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const float pc = fminf(fmaxf(f[y][x], 0.0f), 255.0f);
-        const float yv = pc + kMagic;
-        maxr = fmaxf(maxr, fabsf(pc - (yv - kMagic)));
-        out[y * kRowBytes + 3 * x] = (uint8_t)(__float_as_uint(yv) & 0xffu);
-      }
-    if (maxr > thr) {
+      for (int y = 0; y < 8; ++y) idct8(f[y]);
+      const float thr = 0.5f - l1 * kGuardInvScale;
+      uint8_t* out = pix + b * 24 + c;
+      uint32_t mlo = 0, mhi = 0;
 #pragma unroll
       for (int y = 0; y < 8; ++y)
 #pragma unroll
@@ -140,48 +134,84 @@ __global__ void __launch_bounds__(kThreads) restore_kernel(const __grid_constant
           const float pc = fminf(fmaxf(f[y][x], 0.0f), 255.0f);
           const float yv = pc + kMagic;
           if (fabsf(pc - (yv - kMagic)) > thr) {
-            const int idx = atomicAdd(&misc[0], 1);
-            if (idx < kQueueCap) {
-              queue[idx] = QEntry{(uint16_t)cb, (uint8_t)(8 * y + x), 0, pc};
-            } else {  // queue full: resolve here
-              int p = resolve_inv(pubst, privst, cb, 8 * y + x, pc, k, a.binv, &n3, &fail);
-              out[y * kRowBytes + 3 * x] = (uint8_t)(p < 0 ? 0 : (p > 255 ? 255 : p));
-            }
+            if (8 * y + x < 32)
+              mlo |= 1u << (8 * y + x);
+            else
+              mhi |= 1u << (8 * y + x - 32);
           }
+          out[y * kRowBytes + 3 * x] = (uint8_t)__float_as_uint(yv);
         }
+      uint64_t mask = ((uint64_t)mhi << 32) | mlo;
+      while (mask) {
+        const int pos = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const int idx = atomicAdd(&misc[0], 1);
+        if (idx < kQueueCap) {
+          queue[idx] = ((uint32_t)cb << 8) | (uint32_t)pos;
+        } else {  // queue full: decide here
+          uint32_t Q[32];
+          int n[9];
+          gather_coefs(pubst, privst, cb, k, Q);
+          coords_inv(Q, pos, a.cinv, n);
+          const int p = exact_round(n, &esc, &fail);
+          out[(pos >> 3) * kRowBytes + 3 * (pos & 7)] = (uint8_t)(p < 0 ? 0 : (p > 255 ? 255 : p));
+        }
+      }
+    }
+    __syncthreads();                                                       // C
+    {
+      const int nq = min(misc[0], kQueueCap);
+      for (int i = t; i < nq; i += kThreads) {
+        const uint32_t e = queue[i];
+        const int ecb = (int)(e >> 8), pos = (int)(e & 255);
+        const int eb = ecb / 3, ec = ecb - 3 * eb;
+        uint32_t Q[32];
+        int n[9];
+        gather_coefs(pubst, privst, ecb, k, Q);
+        coords_inv(Q, pos, a.cinv, n);
+        const int p = exact_round(n, &esc, &fail);
+        pix[(pos >> 3) * kRowBytes + eb * 24 + 3 * (pos & 7) + ec] = (uint8_t)(p < 0 ? 0 : (p > 255 ? 255 : p));
+      }
+      if (t == 0) misc[1] += misc[0];
+    }
+    __syncthreads();                                                       // D
+    for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
+      const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
+      const int bb = rem / 3, q = rem - 3 * bb;
+      if (bb < nb)
+        *reinterpret_cast<uint2*>(a.pixels_out + blk[bb] + y * w3 + 8 * q) =
+            *reinterpret_cast<const uint2*>(pix + y * kRowBytes + bb * 24 + 8 * q);
     }
   }
+  if (esc) atomicAdd(&misc[2], esc);
+  if (fail) atomicAdd(&misc[3], 1);
   __syncthreads();
-  const int nq = min(misc[0], kQueueCap);
-  for (int i = t; i < nq; i += kThreads) {
-    const QEntry e = queue[i];
-    const int eb = e.cb / 3, ec = e.cb - 3 * eb;
-    const int p = resolve_inv(pubst, privst, e.cb, e.pos, e.v, k, a.binv, &n3, &fail);
-    tile[(e.pos >> 3) * kRowBytes + eb * 24 + 3 * (e.pos & 7) + ec] =
-        (uint8_t)(p < 0 ? 0 : (p > 255 ? 255 : p));
+  if (t == 0 && a.counters) {
+    if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
+    if (misc[2]) atomicAdd(&a.counters[1], (unsigned long long)misc[2]);
+    if (misc[3]) atomicAdd(&a.counters[2], (unsigned long long)misc[3]);
   }
-  if (n3) atomicAdd(&misc[1], n3);
-  if (fail) atomicAdd(&misc[2], 1);
-  __syncthreads();
-  for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
-    const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
-    const int bb = rem / 3, q = rem - 3 * bb;
-    if (bb < nb)
-      *reinterpret_cast<uint2*>(a.pixels_out + blk[bb] + y * w3 + 8 * q) =
-          *reinterpret_cast<const uint2*>(tile + y * kRowBytes + bb * 24 + 8 * q);
-  }
-  tile_epilogue_counters(a, smem);
 }
 
-cudaError_t launch_restore(const TileArgs& a, cudaStream_t s) {
-  const int grid = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
-  if (a.k == 0)
-    restore_kernel<0><<<grid, kThreads, kSmemBytes, s>>>(a);
-  else if (a.k == 5)
-    restore_kernel<5><<<grid, kThreads, kSmemBytes, s>>>(a);
-  else
-    restore_kernel<-1><<<grid, kThreads, kSmemBytes, s>>>(a);
+template <int K>
+static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(restore_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
+  const int grid = ntiles < kCtasPerSm * sms ? ntiles : kCtasPerSm * sms;
+  restore_kernel<K><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms) {
+  if (a.k == 0) return launch_k<0>(a, s, sms);
+  if (a.k == 5) return launch_k<5>(a, s, sms);
+  return launch_k<-1>(a, s, sms);
 }
 
 }  // namespace fds

@@ -1,11 +1,14 @@
 // Tile machinery shared by the fused protect and restore kernels.
 //
-// Work decomposition: one CTA per tile of 64 consecutive 8x8 pixel blocks (row-major over an
-// image's block grid), one thread per channel-block (cb = 3 * block + channel, 192 threads).
+// Work decomposition: a tile is 64 consecutive 8x8 pixel blocks (row-major over an image's
+// block grid); one thread per channel-block (cb = 3 * block + channel, 192 threads per CTA).
 // A tile's public and private outputs are contiguous, 16-byte aligned byte ranges
-// (64 blocks x 3 channels x 2(63-k) or 2(k+1) bytes), so the tile stages them in shared
-// memory and moves them with coalesced 16-byte accesses; the tile's private range is also a
-// whole number of AES blocks, so CTR needs no data from neighbouring tiles.
+// (64 blocks x 3 channels x 2(63-k) or 2(k+1) bytes), so a tile stages them in shared memory
+// and moves them with 16-byte (or bulk) copies; the tile's private range is a whole number of
+// AES blocks, so CTR needs nothing from neighbouring tiles.
+//
+// The kernels are persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// and prefetches the next tile's input with cp.async while it transforms the current one.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,20 +18,14 @@
 
 namespace fds {
 
-constexpr int kTileBlocks = 64;                // pixel blocks per CTA
-constexpr int kTileCb = 3 * kTileBlocks;       // channel-blocks per CTA
+constexpr int kTileBlocks = 64;                // pixel blocks per tile
+constexpr int kTileCb = 3 * kTileBlocks;       // channel-blocks per tile
 constexpr int kThreads = kTileCb;              // one thread per channel-block
 constexpr int kRowBytes = kTileBlocks * 24;    // one pixel row of the tile (8 px x 3 ch per block)
-constexpr int kPixBytes = 8 * kRowBytes;
+constexpr int kPixBytes = 8 * kRowBytes;       // 12 KB
 constexpr int kCoefBytes = kTileCb * 128;      // public + private int16 staging (64 per cb)
-constexpr int kQueueCap = 256;                 // near-tie entries per CTA
-constexpr int kSmemPix = 0;
-constexpr int kSmemCoef = kSmemPix + kPixBytes;
-constexpr int kSmemT0 = kSmemCoef + kCoefBytes;
-constexpr int kSmemQueue = kSmemT0 + 1024;
-constexpr int kSmemBlk = kSmemQueue + 8 * kQueueCap;
-constexpr int kSmemMisc = kSmemBlk + 8 * kTileBlocks;
-constexpr int kSmemBytes = kSmemMisc + 16;
+constexpr int kQueueCap = 256;                 // near-tie entries per tile
+constexpr int kCtasPerSm = 2;
 
 // Forward guard.  On level-shifted pixels |p - 128| <= 128 the butterflies are within
 // 1.11e-3 of the exact coefficient (first-order bound: every rounded operation and every
@@ -36,10 +33,6 @@ constexpr int kSmemBytes = kSmemMisc + 16;
 constexpr float kGuardFwd = 1.0f / 512.0f;
 // Inverse guard per channel-block: error <= 2.89 u sum|F| (u = 2^-24); 2^-22 sum|F| is used.
 constexpr float kGuardInvScale = 1.0f / 4194304.0f;
-
-// stage-2 tables hold round(8 b_u(y) b_v(x) 2^28); forward [8u+v][8y+x], inverse
-// [8y+x][zigzag(u, v)]
-constexpr int kFixShift = 28;
 
 struct TileArgs {
   const uint8_t* pixels_in;
@@ -49,90 +42,51 @@ struct TileArgs {
   const uint8_t* priv_in;
   uint8_t* priv_out;
   float* dbg_coefs;               // protect debug export, or null
-  const uint32_t* T0;             // AES T-table, 256 words (device)
-  const int32_t* bfwd;            // stage-2 tables (device)
-  const int32_t* binv;
+  const uint32_t* T;              // AES T-tables, 4 x 256 words (device)
+  const uint32_t* cfwd;           // exact-coordinate tables (device), see fds_api.cu
+  const uint32_t* cinv;
   unsigned long long* counters;   // 3 counters (device)
   int32_t width, bx_count, nblocks, k;
   uint64_t iv_hi, iv_lo;          // initial counter block, big-endian halves
   uint32_t rk[44];                // AES-128 round keys
 };
 
-struct QEntry {
-  uint16_t cb;   // channel-block within the tile
-  uint8_t pos;   // coefficient 8u+v (protect) or pixel 8y+x (restore)
-  uint8_t pad;
-  float v;       // float32 value near a half-integer
-};
+// launchers (one translation unit each); `sms` = number of SMs of the device
+cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms);
+cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms);
 
-// launchers (one translation unit each)
-cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug);
-cudaError_t launch_restore(const TileArgs& a, cudaStream_t s);
-
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// bulk (TMA engine) copies shared -> global; sizes and addresses multiples of 16
+__device__ __forceinline__ void bulk_store(void* gmem, const void* smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gmem),
+               "r"(smem_u32(smem)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// make this thread's generic-proxy shared-memory writes visible to later bulk copies
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
-// round-half-away choice between m = floor(v) and m + 1 from the sign of value - (m + 1/2)
-__device__ __forceinline__ int pick(int m, int sgn) {
-  return sgn > 0 ? m + 1 : (sgn < 0 ? m : (m >= 0 ? m + 1 : m));
-}
-
-// coefficient at zigzag index z of tile channel-block cb (int16 staging)
-__device__ __forceinline__ int coef_at(const int16_t* pubst, const int16_t* privst, int cb, int z,
-                                       int k) {
-  return z <= k ? privst[cb * (k + 1) + z] : pubst[cb * (63 - k) + z - k - 1];
-}
-
-// block source offsets, T0 table and per-CTA counters
-__device__ __forceinline__ void tile_prologue(const TileArgs& a, uint8_t* smem, int b0, int nb) {
-  uint64_t* blk = reinterpret_cast<uint64_t*>(smem + kSmemBlk);
-  uint32_t* T0s = reinterpret_cast<uint32_t*>(smem + kSmemT0);
-  int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
-  const int t = threadIdx.x;
-  if (t < nb) {
-    const int gb = b0 + t;
-    const int by = gb / a.bx_count, bx = gb - by * a.bx_count;
-    blk[t] = (uint64_t)by * 8ull * (uint64_t)a.width * 3ull + (uint64_t)bx * 24ull;
-  }
-  if (t < 4) misc[t] = 0;
-  for (int i = t; i < 256; i += kThreads) T0s[i] = a.T0[i];
-}
-
-__device__ __forceinline__ void tile_epilogue_counters(const TileArgs& a, uint8_t* smem) {
-  const int* misc = reinterpret_cast<const int*>(smem + kSmemMisc);
-  if (threadIdx.x == 0 && a.counters) {
-    if (misc[0]) atomicAdd(&a.counters[0], (unsigned long long)misc[0]);
-    if (misc[1]) atomicAdd(&a.counters[1], (unsigned long long)misc[1]);
-    if (misc[2]) atomicAdd(&a.counters[2], (unsigned long long)misc[2]);
-  }
-}
-
-// AES-128-CTR over `bytes` bytes of a 16-byte aligned staging area whose first byte is byte
-// 16 * first_block of the image's private message.
-__device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_block,
-                                         const TileArgs& a, const uint32_t* T0s) {
-  const int nblk = (bytes + 15) >> 4;
-  for (int i = threadIdx.x; i < nblk; i += kThreads) {
-    uint32_t s[4];
-    ctr_block(a.iv_hi, a.iv_lo, first_block + i, s);
-    aes128_encrypt(s, a.rk, T0s);
-    uint4* p = reinterpret_cast<uint4*>(st + 16 * i);
-    uint4 d = *p;
-    d.x ^= s[0];
-    d.y ^= s[1];
-    d.z ^= s[2];
-    d.w ^= s[3];
-    *p = d;
-  }
+// byte offset of block gb's top-left pixel in an H x W x 3 image
+__device__ __forceinline__ uint64_t block_offset(const TileArgs& a, int gb) {
+  const int by = gb / a.bx_count, bx = gb - by * a.bx_count;
+  return (uint64_t)by * 8ull * (uint64_t)a.width * 3ull + (uint64_t)bx * 24ull;
 }
 
 // 24-byte block row of the pixel tile shifted right by `c` bytes: channel c's pixel x is
@@ -144,6 +98,82 @@ __device__ __forceinline__ void load_row_shifted(const uint8_t* tile, int y, int
   const uint32_t r[7] = {w01.x, w01.y, w23.x, w23.y, w45.x, w45.y, 0u};
 #pragma unroll
   for (int i = 0; i < 6; ++i) w[i] = __funnelshift_r(r[i], r[i + 1], 8 * c);
+}
+
+// AES-128-CTR over `bytes` bytes of a 16-byte aligned staging area whose first byte is byte
+// 16 * first_block of the image's private message.
+__device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_block,
+                                         const TileArgs& a, const uint32_t* Ts) {
+  const int nblk = (bytes + 15) >> 4;
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+    uint32_t s[4];
+    ctr_block(a.iv_hi, a.iv_lo, first_block + i, s);
+    aes128_encrypt(s, a.rk, Ts);
+    uint4* p = reinterpret_cast<uint4*>(st + 16 * i);
+    uint4 d = *p;
+    d.x ^= s[0];
+    d.y ^= s[1];
+    d.z ^= s[2];
+    d.w ^= s[3];
+    *p = d;
+  }
+}
+
+// Exact integer coordinates of 8 F[u][v] (pos = 8u+v) of channel c of tile block b:
+// n[j] = sum over the 64 pixels of pixel * K_j, with the signed-byte weights K_j of
+// table[pos][j][16 words] (word w covers pixels x = 4(w&1) .. +3 of row w>>1).
+__device__ __forceinline__ void coords_fwd(const uint8_t* tile, int b, int c, int pos,
+                                           const uint32_t* table, int (&n)[9]) {
+  uint32_t P[16];
+#pragma unroll
+  for (int y = 0; y < 8; ++y) {
+    uint32_t w[6];
+    load_row_shifted(tile, y, b, c, w);
+    // bytes 0, 3, 6, 9 and 12, 15, 18, 21 of w
+    P[2 * y] = __byte_perm(__byte_perm(w[0], w[1], 0x0630u), w[2], 0x5210u);
+    P[2 * y + 1] = __byte_perm(__byte_perm(w[3], w[4], 0x0630u), w[5], 0x5210u);
+  }
+  const uint4* t4 = reinterpret_cast<const uint4*>(table + pos * 128);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int acc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 tw = __ldg(t4 + 4 * j + q);
+      acc = dp4a_us(P[4 * q + 0], tw.x, acc);
+      acc = dp4a_us(P[4 * q + 1], tw.y, acc);
+      acc = dp4a_us(P[4 * q + 2], tw.z, acc);
+      acc = dp4a_us(P[4 * q + 3], tw.w, acc);
+    }
+    n[j] = acc;
+  }
+  n[8] = 0;
+}
+
+// Exact integer coordinates of 8 p[y][x] (pos = 8y+x) from int16 coefficients in zigzag
+// order, packed two per word (Q[i] = q(2i) | q(2i+1) << 16), with the weights of
+// table[pos][j][16 words] (word t covers zigzag indices 4t .. 4t+3).
+__device__ __forceinline__ void coords_inv(const uint32_t (&Q)[32], int pos, const uint32_t* table,
+                                           int (&n)[9]) {
+  const uint4* t4 = reinterpret_cast<const uint4*>(table + pos * 128);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int acc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 tw = __ldg(t4 + 4 * j + q);
+      acc = dp2a_lo(Q[8 * q + 0], tw.x, acc);
+      acc = dp2a_hi(Q[8 * q + 1], tw.x, acc);
+      acc = dp2a_lo(Q[8 * q + 2], tw.y, acc);
+      acc = dp2a_hi(Q[8 * q + 3], tw.y, acc);
+      acc = dp2a_lo(Q[8 * q + 4], tw.z, acc);
+      acc = dp2a_hi(Q[8 * q + 5], tw.z, acc);
+      acc = dp2a_lo(Q[8 * q + 6], tw.w, acc);
+      acc = dp2a_hi(Q[8 * q + 7], tw.w, acc);
+    }
+    n[j] = acc;
+  }
+  n[8] = 0;
 }
 
 }  // namespace fds

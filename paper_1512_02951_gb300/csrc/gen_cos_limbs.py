@@ -6,6 +6,9 @@ They are computed here from the Taylor series of cos, with pi from Machin's form
 pi = 16 atan(1/5) - 4 atan(1/239), all in integer fixed point with 64 guard bits, then
 truncated to 256 fractional bits (each value within one unit of 2^-256).
 
+It also writes round(cos(j pi / 16) * 2^62), j = 1..7, for the 128-bit first try of the
+same decision.
+
 Run:  python gen_cos_limbs.py > fds_cos_limbs.h
 """
 FRAC = 256
@@ -53,6 +56,10 @@ def main():
         limbs = [(v >> (32 * i)) & 0xFFFFFFFF for i in range(8)]
         print("    {" + ", ".join("0x%08xu" % t for t in limbs) + "}, /* j = %d */ \\" % j)
     print("  }")
+    print("/* round(cos(j pi/16) * 2^62), j = 1..7 */")
+    q62 = [(cos_fixed(j) + (1 << (S - 63))) >> (S - 62) for j in range(1, 8)]
+    print("#define FDS_COS_Q62_INIT \\")
+    print("  {" + ", ".join("%dll" % v for v in q62) + "}")
 
 
 if __name__ == "__main__":

@@ -220,3 +220,41 @@ def test_4096_full_size_sampled(api, k):
         assert np.array_equal(back[8 * r0: 8 * r1], want)
     frac = np.mean(back == img)
     assert 0.88 < frac < 0.97
+
+
+def test_queue_overflow_forward(api):
+    # a block with exact ties at several irrational positions, repeated over whole tiles, puts
+    # more near-ties into one tile than its queue holds
+    from oracle import exact
+    rng = np.random.default_rng(77)
+    cand = rng.integers(0, 3, (400000, 8, 8))
+    best, best_n = None, 0
+    for (u, v) in [(2, 2)]:
+        n = np.einsum("myx,yxj->mj", cand, exact.K[u, v])
+        hit = np.nonzero((n[:, 1:] == 0).all(axis=1) & (n[:, 0] % 8 == 4))[0]
+    for i in hit[:200]:
+        f = odct.dct2(cand[i])
+        cnt = int((np.abs(f - np.floor(f) - 0.5) < 1e-9).sum())
+        if cnt > best_n:
+            best, best_n = cand[i], cnt
+    assert best_n >= 2
+    blocks = np.broadcast_to(best.astype(np.uint8), (8, 64, 3, 8, 8))
+    img = odct.blocks_to_image(np.ascontiguousarray(blocks))
+    api.counters(reset=True)
+    _check_image(api, img, 5, seed=11)
+    assert api.counters()[0] > 8 * 64 * 3 * best_n // 2
+
+
+def test_queue_overflow_inverse(api):
+    # DC-only coefficient blocks with DC = 4 (mod 8): every pixel is an exact .5
+    w, h, k = 512, 16, 0
+    by, bx = h // 8, w // 8
+    rng = np.random.default_rng(5)
+    pub = np.zeros((by, bx, 3, 63 - k), dtype=np.int16)
+    plain = (8 * rng.integers(0, 255, (by, bx, 3, k + 1)) + 4).astype("<i2")
+    plain[0, :8, :, 0] = -4 - 8 * np.arange(8)[:, None]        # negative ties, clamped to 0
+    key, iv = synth.make_key(15), synth.make_iv(16)
+    priv = oaes.ctr_xcrypt(key, iv, plain.tobytes())
+    got = _gpu_restore(api, pub, priv, w, h, k, key, iv)
+    want = ofds.restore(pub, priv, key, iv, k, w, h)
+    assert np.array_equal(got, want)
