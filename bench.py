@@ -363,7 +363,7 @@ def gpu_arm(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
             "quality": {"exact_restore_fraction": round(exact_frac, 5), "psnr_db": round(psnr, 3),
-                        "fixed_point_redecisions": n2, "exact_decisions": n3, "failures": fails},
+                        "exact_redecisions": n2, "escalations_256bit": n3, "failures": fails},
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -119,9 +119,11 @@ int fds_restore(const int16_t* public_in, const uint8_t* private_in, uint8_t* pi
 int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
                       float* coefs_out, void* stream);
 
-/* Diagnostics: counters of the exact-rounding fallbacks taken since the last reset,
- * out[0] = values re-decided in 64-bit fixed point, out[1] = values decided in exact
- * algebraic arithmetic, out[2] = internal consistency failures (must stay 0).
+/* Diagnostics: counters of the exact-rounding fallbacks taken since the last reset:
+ * out[0] = values within the float32 error guard of a rounding boundary, re-decided from
+ * their exact integer coordinates in Z[cos(pi/16)]; out[1] = of those, values whose 128-bit
+ * fixed-point evaluation was still ambiguous and that a 256-bit evaluation decided (exact
+ * ties excluded); out[2] = internal consistency failures (must stay 0).
  * Host pointer to 3 uint64.  Synchronises the device.  reset != 0 clears them. */
 int fds_counters(uint64_t* out, int reset);
 

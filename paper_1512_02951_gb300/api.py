@@ -160,7 +160,7 @@ def debug_dct_f32(pixels: torch.Tensor) -> torch.Tensor:
 
 
 def counters(reset: bool = False) -> tuple[int, int, int]:
-    """fds_counters: (fixed-point re-decisions, exact-arithmetic decisions, failures)."""
+    """fds_counters: (exact re-decisions, 256-bit escalations among them, failures)."""
     out = (ctypes.c_uint64 * 3)()
     _lib.check(_lib.load().fds_counters(out, 1 if reset else 0), "fds_counters")
     return int(out[0]), int(out[1]), int(out[2])

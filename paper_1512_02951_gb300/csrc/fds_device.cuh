@@ -159,33 +159,34 @@ __host__ __device__ inline uint32_t aes_t0(uint8_t x) {
 // round takes S[x] from byte 1 of T[0][x].
 __device__ __forceinline__ void aes128_encrypt(uint32_t (&s)[4], const uint32_t* rk,
                                                const uint32_t* T) {
-  const uint32_t* T0 = T;
-  const uint32_t* T1 = T + 256;
-  const uint32_t* T2 = T + 512;
-  const uint32_t* T3 = T + 768;
+  // table entry by byte offset: byte b of a word, times 4, is (w >> (8b - 2)) & 0x3fc
+  const char* Tc = reinterpret_cast<const char*>(T);
+  auto t0 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + ((w << 2) & 0x3fcu)); };
+  auto t1 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + 1024 + ((w >> 6) & 0x3fcu)); };
+  auto t2 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + 2048 + ((w >> 14) & 0x3fcu)); };
+  auto t3 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + 3072 + ((w >> 22) & 0x3fcu)); };
   uint32_t s0 = s[0] ^ rk[0], s1 = s[1] ^ rk[1], s2 = s[2] ^ rk[2], s3 = s[3] ^ rk[3];
 #pragma unroll
   for (int r = 1; r < 10; ++r) {
-    const uint32_t t0 = T0[s0 & 0xff] ^ T1[(s1 >> 8) & 0xff] ^ T2[(s2 >> 16) & 0xff] ^ T3[s3 >> 24] ^ rk[4 * r];
-    const uint32_t t1 = T0[s1 & 0xff] ^ T1[(s2 >> 8) & 0xff] ^ T2[(s3 >> 16) & 0xff] ^ T3[s0 >> 24] ^ rk[4 * r + 1];
-    const uint32_t t2 = T0[s2 & 0xff] ^ T1[(s3 >> 8) & 0xff] ^ T2[(s0 >> 16) & 0xff] ^ T3[s1 >> 24] ^ rk[4 * r + 2];
-    const uint32_t t3 = T0[s3 & 0xff] ^ T1[(s0 >> 8) & 0xff] ^ T2[(s1 >> 16) & 0xff] ^ T3[s2 >> 24] ^ rk[4 * r + 3];
-    s0 = t0;
-    s1 = t1;
-    s2 = t2;
-    s3 = t3;
+    const uint32_t n0 = t0(s0) ^ t1(s1) ^ t2(s2) ^ t3(s3) ^ rk[4 * r];
+    const uint32_t n1 = t0(s1) ^ t1(s2) ^ t2(s3) ^ t3(s0) ^ rk[4 * r + 1];
+    const uint32_t n2 = t0(s2) ^ t1(s3) ^ t2(s0) ^ t3(s1) ^ rk[4 * r + 2];
+    const uint32_t n3 = t0(s3) ^ t1(s0) ^ t2(s1) ^ t3(s2) ^ rk[4 * r + 3];
+    s0 = n0;
+    s1 = n1;
+    s2 = n2;
+    s3 = n3;
   }
-  // last round: SubBytes + ShiftRows + AddRoundKey; byte r of column c = S[row r of column c+r]
-  // (__byte_perm selector 0x4441 etc. moves byte 1 of T0[x] to byte r, zeroing the rest)
-  auto sb = [&](uint32_t idx, uint32_t sel) { return __byte_perm(T0[idx], 0u, sel); };
-  s[0] = (sb(s0 & 0xff, 0x4441u) | sb((s1 >> 8) & 0xff, 0x4414u) | sb((s2 >> 16) & 0xff, 0x4144u) |
-          sb(s3 >> 24, 0x1444u)) ^ rk[40];
-  s[1] = (sb(s1 & 0xff, 0x4441u) | sb((s2 >> 8) & 0xff, 0x4414u) | sb((s3 >> 16) & 0xff, 0x4144u) |
-          sb(s0 >> 24, 0x1444u)) ^ rk[41];
-  s[2] = (sb(s2 & 0xff, 0x4441u) | sb((s3 >> 8) & 0xff, 0x4414u) | sb((s0 >> 16) & 0xff, 0x4144u) |
-          sb(s1 >> 24, 0x1444u)) ^ rk[42];
-  s[3] = (sb(s3 & 0xff, 0x4441u) | sb((s0 >> 8) & 0xff, 0x4414u) | sb((s1 >> 16) & 0xff, 0x4144u) |
-          sb(s2 >> 24, 0x1444u)) ^ rk[43];
+  // last round: SubBytes + ShiftRows + AddRoundKey; byte r of column c = S[row r of column c+r];
+  // S[x] is byte 1 of T0[x] (__byte_perm selector 0x4441 etc. moves it to byte r)
+  s[0] = (__byte_perm(t0(s0), 0u, 0x4441u) | __byte_perm(t0(s1 >> 8), 0u, 0x4414u) |
+          __byte_perm(t0(s2 >> 16), 0u, 0x4144u) | __byte_perm(t0(s3 >> 24), 0u, 0x1444u)) ^ rk[40];
+  s[1] = (__byte_perm(t0(s1), 0u, 0x4441u) | __byte_perm(t0(s2 >> 8), 0u, 0x4414u) |
+          __byte_perm(t0(s3 >> 16), 0u, 0x4144u) | __byte_perm(t0(s0 >> 24), 0u, 0x1444u)) ^ rk[41];
+  s[2] = (__byte_perm(t0(s2), 0u, 0x4441u) | __byte_perm(t0(s3 >> 8), 0u, 0x4414u) |
+          __byte_perm(t0(s0 >> 16), 0u, 0x4144u) | __byte_perm(t0(s1 >> 24), 0u, 0x1444u)) ^ rk[42];
+  s[3] = (__byte_perm(t0(s3), 0u, 0x4441u) | __byte_perm(t0(s0 >> 8), 0u, 0x4414u) |
+          __byte_perm(t0(s1 >> 16), 0u, 0x4144u) | __byte_perm(t0(s2 >> 24), 0u, 0x1444u)) ^ rk[43];
 }
 
 // Counter block IV + n (128-bit big-endian addition) as four state columns.

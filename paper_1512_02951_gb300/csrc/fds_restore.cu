@@ -3,22 +3,21 @@
 // position, inverse 8x8 DCT, round half away from zero (exact), clamp to [0, 255].
 //
 // Persistent CTAs; per tile (see fds_tile.cuh for the decomposition):
-//   A. the tile's fragment ranges (prefetched with cp.async during the previous tile) are in
-//      shared memory; the next tile's start loading
-//   1. AES-128-CTR decryption of the private range in place
-//   B. 2. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
+//   A. the tile's fragments are in shared memory, already decrypted; the next tile's start
+//      loading (cp.async)
+//   1. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
 //      into the interleaved pixel tile; values within the float32 error guard of a
 //      half-integer are queued
-//   C. 3. queued pixels are re-decided exactly (integer coordinates in Z[cos(pi/16)])
-//   D. 4. the pixel tile goes to global memory with 8-byte stores
+//   B. 2. queued pixels are re-decided exactly (integer coordinates in Z[cos(pi/16)])
+//   C. 3. the pixel tile goes to global memory with 8-byte stores, and the next tile's
+//      private range is decrypted in place (AES-128-CTR)
 #include "fds_tile.cuh"
 
 namespace fds {
 
 constexpr int kSmemCoef = 0;                                 // 2 fragment staging areas
 constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 1 pixel tile
-constexpr int kSmemT = kSmemPix + kPixBytes;                 // AES tables, 4 KB
-constexpr int kSmemQueue = kSmemT + 4096;
+constexpr int kSmemQueue = kSmemPix + kPixBytes;
 constexpr int kSmemBlk = kSmemQueue + 4 * kQueueCap;
 constexpr int kSmemMisc = kSmemBlk + 8 * kTileBlocks;
 constexpr int kSmemBytes = kSmemMisc + 32;
@@ -39,8 +38,8 @@ __device__ __forceinline__ void gather_coefs(const int16_t* pubst, const int16_t
 template <int K>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(16) uint32_t Ts[1024];                // AES T-tables
   uint8_t* pix = smem + kSmemPix;
-  uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
   uint64_t* blk = reinterpret_cast<uint64_t*>(smem + kSmemBlk);
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
@@ -78,7 +77,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     cp_async_commit();
   };
 
+  auto decrypt = [&](int tl, int buf) {
+    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
+    uint8_t* vst = smem + kSmemCoef + buf * kCoefBytes + kTileCb * 2 * npub;
+    ctr_tile(vst, nbl * 6 * (k + 1), ((uint64_t)tl * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, a, Ts);
+  };
+
   issue_frag(tile, 0);
+  cp_async_wait_all();
+  __syncthreads();
+  decrypt(tile, 0);
   int it = 0;
   int esc = 0;
   bool fail = false;
@@ -86,17 +94,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     const int buf = it & 1;
     const int next = tile + gridDim.x;
     const int nb = min(kTileBlocks, a.nblocks - tile * kTileBlocks);
-    cp_async_wait_all();
     if (t == 0) misc[0] = 0;
     __syncthreads();                                                       // A
     if (next < ntiles) issue_frag(next, buf ^ 1);
     if (t < nb) blk[t] = block_offset(a, tile * kTileBlocks + t);
-    uint8_t* st = smem + kSmemCoef + buf * kCoefBytes;
+    const uint8_t* st = smem + kSmemCoef + buf * kCoefBytes;
     const int16_t* pubst = reinterpret_cast<const int16_t*>(st);
-    int16_t* privst = reinterpret_cast<int16_t*>(st + kTileCb * 2 * npub);
-    ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
-             ((uint64_t)tile * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, a, Ts);
-    __syncthreads();                                                       // B
+    const int16_t* privst = reinterpret_cast<const int16_t*>(st + kTileCb * 2 * npub);
 
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
     if (b < nb) {
@@ -158,7 +162,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         }
       }
     }
-    __syncthreads();                                                       // C
+    cp_async_wait_all();                                  // this thread's copies of `next`
+    __syncthreads();                                                       // B
     {
       const int nq = min(misc[0], kQueueCap);
       for (int i = t; i < nq; i += kThreads) {
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       }
       if (t == 0) misc[1] += misc[0];
     }
-    __syncthreads();                                                       // D
+    __syncthreads();                                                       // C
     for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
       const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
       const int bb = rem / 3, q = rem - 3 * bb;
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         *reinterpret_cast<uint2*>(a.pixels_out + blk[bb] + y * w3 + 8 * q) =
             *reinterpret_cast<const uint2*>(pix + y * kRowBytes + bb * 24 + 8 * q);
     }
+    if (next < ntiles) decrypt(next, buf ^ 1);
   }
   if (esc) atomicAdd(&misc[2], esc);
   if (fail) atomicAdd(&misc[3], 1);
