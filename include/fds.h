@@ -113,6 +113,53 @@ int fds_protect(const uint8_t* pixels, int16_t* public_out, uint8_t* private_out
 int fds_restore(const int16_t* public_in, const uint8_t* private_in, uint8_t* pixels_out,
                 const fds_image* images, int32_t n, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched form: a plan holds a batch's descriptors and tile schedule in device memory, so
+ * that the whole batch runs as ONE persistent launch (every 64-block tile of every image
+ * in one grid), optionally captured in a CUDA graph.  Work is the same per image as
+ * fds_protect_image / fds_restore_image and so are the outputs, bit for bit.
+ */
+typedef struct fds_plan fds_plan;
+
+/* Create a plan for n images (host descriptor array, keys by registered slot).  Allocates
+ * the plan's device memory (descriptors, tile prefix sums, a tile counter) on the current
+ * device.  The key slots must stay registered while the plan is used. */
+int fds_plan_create(const fds_image* images, int32_t n, fds_plan** plan_out);
+
+/* Free a plan (synchronises the device first). */
+int fds_plan_destroy(fds_plan* plan);
+
+/* Schedule of the persistent launch.  ctas_per_sm: 1 or 2 resident CTAs per SM;
+ * dynamic: 0 = static round-robin tile assignment, 1 = tiles handed out by an atomic
+ * counter; largest_first: 0 = tiles in descriptor order, 1 = images by decreasing size.
+ * Re-uploads the schedule and drops captured graphs. */
+int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic,
+                          int32_t largest_first);
+
+/* Read the current schedule (host pointers, each may be NULL). */
+int fds_plan_get_schedule(const fds_plan* plan, int32_t* ctas_per_sm, int32_t* dynamic,
+                          int32_t* largest_first);
+
+/* Time every schedule on this batch (protect, `reps` launches each, on `stream`) and keep
+ * the fastest.  The buffers are written to; their previous contents are lost. */
+int fds_plan_autotune(fds_plan* plan, const uint8_t* pixels, int16_t* public_out,
+                      uint8_t* private_out, int32_t reps, void* stream);
+
+/* One persistent launch protecting / restoring every image of the plan.  Buffer pointers
+ * and offsets as for fds_protect / fds_restore. */
+int fds_plan_protect(fds_plan* plan, const uint8_t* pixels, int16_t* public_out,
+                     uint8_t* private_out, void* stream);
+int fds_plan_restore(fds_plan* plan, const int16_t* public_in, const uint8_t* private_in,
+                     uint8_t* pixels_out, void* stream);
+
+/* The same through a CUDA graph: the first call (or a call with other buffers) captures
+ * the counter reset and the launch into a graph owned by the plan; later calls replay it.
+ * The first call must not be inside another stream capture. */
+int fds_plan_protect_graph(fds_plan* plan, const uint8_t* pixels, int16_t* public_out,
+                           uint8_t* private_out, void* stream);
+int fds_plan_restore_graph(fds_plan* plan, const int16_t* public_in, const uint8_t* private_in,
+                           uint8_t* pixels_out, void* stream);
+
 /* Diagnostics: the float32 coefficients the protect kernel computes before rounding, as
  * float [H/8][W/8][3][8][8] ([u][v] inside a block).  coefs_out: device.  Used to compare
  * the pre-rounding values with a float64 reference (Sect. 6.4.3 precision concern). */

@@ -50,6 +50,20 @@ SIGNATURES = {
                                    ctypes.POINTER(FdsImage), ctypes.c_int32, ctypes.c_void_p]),
     "fds_restore": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(FdsImage), ctypes.c_int32, ctypes.c_void_p]),
+    "fds_plan_create": (ctypes.c_int, [ctypes.POINTER(FdsImage), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "fds_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fds_plan_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32]),
+    "fds_plan_get_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]),
+    "fds_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "fds_plan_protect": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "fds_plan_restore": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "fds_plan_protect_graph": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "fds_plan_restore_graph": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "fds_debug_dct_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "fds_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),

@@ -169,3 +169,53 @@ def counters(reset: bool = False) -> tuple[int, int, int]:
 def sync() -> None:
     """fds_sync on the current stream."""
     _lib.check(_lib.load().fds_sync(_stream_ptr(torch.device("cuda"))), "fds_sync")
+
+
+class Plan:
+    """fds_plan_*: a batch whose descriptors and tile schedule live on the device, run as one
+    persistent launch (optionally through a CUDA graph)."""
+
+    def __init__(self, descs: Sequence[ImageDesc]):
+        arr = _desc_array(descs)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().fds_plan_create(arr, len(descs), ctypes.byref(h)), "fds_plan_create")
+        self._h = h
+        self.descs = list(descs)
+
+    def close(self) -> None:
+        if self._h:
+            _lib.load().fds_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_schedule(self, ctas_per_sm: int = 2, dynamic: bool = False,
+                     largest_first: bool = False) -> None:
+        _lib.check(_lib.load().fds_plan_set_schedule(self._h, ctas_per_sm, int(dynamic),
+                                                     int(largest_first)), "fds_plan_set_schedule")
+
+    def schedule(self) -> tuple[int, int, int]:
+        v = [ctypes.c_int32() for _ in range(3)]
+        _lib.check(_lib.load().fds_plan_get_schedule(self._h, *(ctypes.byref(x) for x in v)),
+                   "fds_plan_get_schedule")
+        return tuple(x.value for x in v)
+
+    def autotune(self, pixels, public_out, private_out, reps: int = 3) -> tuple[int, int, int]:
+        _lib.check(_lib.load().fds_plan_autotune(self._h, pixels.data_ptr(), public_out.data_ptr(),
+                                                 private_out.data_ptr(), reps,
+                                                 _stream_ptr(pixels.device)), "fds_plan_autotune")
+        return self.schedule()
+
+    def protect(self, pixels, public_out, private_out, graph: bool = False) -> None:
+        fn = _lib.load().fds_plan_protect_graph if graph else _lib.load().fds_plan_protect
+        _lib.check(fn(self._h, pixels.data_ptr(), public_out.data_ptr(), private_out.data_ptr(),
+                      _stream_ptr(pixels.device)), "fds_plan_protect")
+
+    def restore(self, public, private, pixels_out, graph: bool = False) -> None:
+        fn = _lib.load().fds_plan_restore_graph if graph else _lib.load().fds_plan_restore
+        _lib.check(fn(self._h, public.data_ptr(), private.data_ptr(), pixels_out.data_ptr(),
+                      _stream_ptr(pixels_out.device)), "fds_plan_restore")

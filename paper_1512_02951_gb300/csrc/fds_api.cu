@@ -7,6 +7,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
+#include <algorithm>
 
 #include "fds.h"
 #include "fds_tile.cuh"
@@ -21,8 +23,10 @@ namespace fds {
 //  g_cinv     the same for the inverse: for pixel 8y+x and coordinate j, the weight of the
 //             coefficient at zigzag index z = 4t + byte (16 words)
 //  g_counters exact-fallback counters
+//  g_rk       round keys of the registered key slots (FDS_MAX_KEYS x 44 words)
 // where 8 b_u(y) b_v(x) = sum_j K_j(u,v,y,x) cos(j pi/16), cos(0) = 1.
 __device__ __align__(16) uint32_t g_T[1024];
+__device__ __align__(16) uint32_t g_rk[FDS_MAX_KEYS * 44];
 __device__ __align__(16) uint32_t g_cfwd[64 * 128];
 __device__ __align__(16) uint32_t g_cinv[64 * 128];
 __device__ unsigned long long g_counters[3];
@@ -49,6 +53,7 @@ struct DevTables {
   const uint32_t* T;
   const uint32_t* cfwd;
   const uint32_t* cinv;
+  const uint32_t* round_keys;
   unsigned long long* counters;
   int sms;
 };
@@ -169,6 +174,12 @@ int ensure_init(int* dev_out = nullptr) {
     return cuda_fail(e, "device attribute");
   if ((e = cudaGetSymbolAddress(&p, g_counters)) != cudaSuccess) return cuda_fail(e, "symbol address");
   tb.counters = static_cast<unsigned long long*>(p);
+  if ((e = cudaGetSymbolAddress(&p, g_rk)) != cudaSuccess) return cuda_fail(e, "symbol address");
+  tb.round_keys = static_cast<const uint32_t*>(p);
+  for (int i = 0; i < FDS_MAX_KEYS; ++i)   // keys registered before this device was ready
+    if (g_slots[i].used &&
+        (e = cudaMemcpyToSymbol(g_rk, g_slots[i].rk, sizeof(g_slots[i].rk), 44 * 4 * i)) != cudaSuccess)
+      return cuda_fail(e, "key upload");
   g_ready[dev] = true;
   return FDS_OK;
 }
@@ -177,21 +188,23 @@ bool bad_dims(int32_t w, int32_t h) {
   return w <= 0 || h <= 0 || (w & 7) || (h & 7) || (int64_t)(w / 8) * (int64_t)(h / 8) > (1ll << 30);
 }
 
-int run_protect(TileArgs& a, int dev, cudaStream_t s, bool debug) {
+void set_tables(TileArgs& a, int dev) {
   a.T = g_tables[dev].T;
   a.cfwd = g_tables[dev].cfwd;
   a.cinv = g_tables[dev].cinv;
+  a.round_keys = g_tables[dev].round_keys;
   a.counters = g_tables[dev].counters;
-  const cudaError_t e = launch_protect(a, s, debug, g_tables[dev].sms);
+}
+
+int run_protect(TileArgs& a, int dev, cudaStream_t s, bool debug, int per_sm = 2) {
+  set_tables(a, dev);
+  const cudaError_t e = launch_protect(a, s, debug, g_tables[dev].sms, per_sm);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "protect launch");
 }
 
-int run_restore(TileArgs& a, int dev, cudaStream_t s) {
-  a.T = g_tables[dev].T;
-  a.cfwd = g_tables[dev].cfwd;
-  a.cinv = g_tables[dev].cinv;
-  a.counters = g_tables[dev].counters;
-  const cudaError_t e = launch_restore(a, s, g_tables[dev].sms);
+int run_restore(TileArgs& a, int dev, cudaStream_t s, int per_sm = 2) {
+  set_tables(a, dev);
+  const cudaError_t e = launch_restore(a, s, g_tables[dev].sms, per_sm);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "restore launch");
 }
 
@@ -222,8 +235,14 @@ int fds_key_register(const uint8_t key[16], int32_t* slot_out) {
   std::lock_guard<std::mutex> lk(g_mu);
   for (int i = 0; i < FDS_MAX_KEYS; ++i) {
     if (!g_slots[i].used) {
-      g_slots[i].used = true;
       expand_key(key, g_slots[i].rk);
+      // device copy now if the current device is initialised, else when it is
+      int dev = -1;
+      if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices && g_ready[dev]) {
+        const cudaError_t e = cudaMemcpyToSymbol(g_rk, g_slots[i].rk, sizeof(g_slots[i].rk), 44 * 4 * i);
+        if (e != cudaSuccess) return cuda_fail(e, "key upload");
+      }
+      g_slots[i].used = true;
       *slot_out = i;
       return FDS_OK;
     }
@@ -389,5 +408,302 @@ int fds_sync(void* stream) {
 }
 
 const char* fds_last_error(void) { return t_err.c_str(); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// batch plans: one persistent launch over every tile of every image
+struct fds_plan {
+  int dev = 0;
+  std::vector<fds_image> images;        // host copy, caller's order
+  int32_t n = 0, total_tiles = 0, k_uniform = -1;
+  int32_t per_sm = 2, dynamic = 0, largest_first = 0;
+  void* mem = nullptr;                  // device: BatchImage[n], tile_start[n+1], counter
+  fds::BatchImage* d_images = nullptr;
+  int32_t* d_tile_start = nullptr;
+  unsigned int* d_dispenser = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // protect, restore
+  const void* graph_bufs[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  cudaStream_t graph_stream[2] = {nullptr, nullptr};
+};
+
+namespace fds {
+namespace {
+
+int check_descs(const fds_image* images, int32_t n) {
+  if (n <= 0 || !images) return set_err(FDS_E_INVALID, "a plan needs at least one image");
+  for (int32_t i = 0; i < n; ++i) {
+    const fds_image& d = images[i];
+    if (bad_dims(d.width, d.height)) return set_err(FDS_E_INVALID, "image " + std::to_string(i) + ": bad size");
+    if (d.k < 0 || d.k > 63) return set_err(FDS_E_INVALID, "image " + std::to_string(i) + ": k out of range");
+    if ((d.pixel_offset & 7) || (d.public_offset & 15) || (d.private_offset & 15))
+      return set_err(FDS_E_INVALID, "image " + std::to_string(i) + ": misaligned offset");
+    if (d.key_slot < 0 || d.key_slot >= FDS_MAX_KEYS || !g_slots[d.key_slot].used)
+      return set_err(FDS_E_NO_KEY, "image " + std::to_string(i) + ": key slot not registered");
+  }
+  return FDS_OK;
+}
+
+void drop_graphs(fds_plan* p) {
+  for (int i = 0; i < 2; ++i) {
+    if (p->graph[i]) cudaGraphExecDestroy(p->graph[i]);
+    p->graph[i] = nullptr;
+  }
+}
+
+// device tables of the plan in its current order
+int upload_schedule(fds_plan* p) {
+  std::vector<int> order(p->n);
+  for (int i = 0; i < p->n; ++i) order[i] = i;
+  if (p->largest_first)
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return (int64_t)p->images[x].width * p->images[x].height > (int64_t)p->images[y].width * p->images[y].height;
+    });
+  std::vector<BatchImage> bi(p->n);
+  std::vector<int32_t> ts(p->n + 1);
+  int64_t acc = 0;
+  for (int j = 0; j < p->n; ++j) {
+    const fds_image& d = p->images[order[j]];
+    BatchImage& b = bi[j];
+    b.pixel_offset = d.pixel_offset;
+    b.public_offset = d.public_offset;
+    b.private_offset = d.private_offset;
+    b.width = d.width;
+    b.height = d.height;
+    b.k = d.k;
+    b.key_slot = d.key_slot;
+    iv_words(d.iv, &b.iv_hi, &b.iv_lo);
+    ts[j] = (int32_t)acc;
+    acc += ((int64_t)(d.width / 8) * (d.height / 8) + kTileBlocks - 1) / kTileBlocks;
+  }
+  if (acc > (1ll << 30)) return set_err(FDS_E_INVALID, "batch too large");
+  ts[p->n] = (int32_t)acc;
+  p->total_tiles = (int32_t)acc;
+  cudaError_t e = cudaMemcpy(p->d_images, bi.data(), sizeof(BatchImage) * p->n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tile_start, ts.data(), sizeof(int32_t) * (p->n + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  drop_graphs(p);
+  return FDS_OK;
+}
+
+int plan_device(const fds_plan* p) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != p->dev) return set_err(FDS_E_INVALID, "the plan belongs to another device");
+  return FDS_OK;
+}
+
+TileArgs plan_args(const fds_plan* p) {
+  TileArgs a{};
+  a.images = p->d_images;
+  a.tile_start = p->d_tile_start;
+  a.n_images = p->n;
+  a.total_tiles = p->total_tiles;
+  a.k = p->k_uniform;
+  a.dispenser = p->dynamic ? p->d_dispenser : nullptr;
+  return a;
+}
+
+// enqueue one protect (dir 0) or restore (dir 1) of the whole plan on s
+int plan_enqueue(fds_plan* p, int dir, const void* b0, const void* b1, const void* b2, cudaStream_t s) {
+  TileArgs a = plan_args(p);
+  if (p->dynamic) {
+    const cudaError_t e = cudaMemsetAsync(p->d_dispenser, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+  }
+  if (dir == 0) {
+    a.pixels_in = static_cast<const uint8_t*>(b0);
+    a.pub_out = static_cast<int16_t*>(const_cast<void*>(b1));
+    a.priv_out = static_cast<uint8_t*>(const_cast<void*>(b2));
+    return run_protect(a, p->dev, s, false, p->per_sm);
+  }
+  a.pub_in = static_cast<const int16_t*>(b0);
+  a.priv_in = static_cast<const uint8_t*>(b1);
+  a.pixels_out = static_cast<uint8_t*>(const_cast<void*>(b2));
+  return run_restore(a, p->dev, s, p->per_sm);
+}
+
+int plan_buffers_ok(const void* px, const void* pub, const void* priv) {
+  if (!px || !priv) return set_err(FDS_E_INVALID, "null buffer");
+  if (misaligned(px, 8) || misaligned(pub, 16) || misaligned(priv, 16))
+    return set_err(FDS_E_INVALID, "misaligned buffer");
+  return FDS_OK;
+}
+
+int plan_graph(fds_plan* p, int dir, const void* b0, const void* b1, const void* b2, cudaStream_t s) {
+  if (s == nullptr) return set_err(FDS_E_INVALID, "graph launches need a created stream, not the default stream");
+  const void* bufs[3] = {b0, b1, b2};
+  if (!p->graph[dir] || std::memcmp(bufs, p->graph_bufs[dir], sizeof(bufs)) != 0) {
+    if (p->graph[dir]) cudaGraphExecDestroy(p->graph[dir]);
+    p->graph[dir] = nullptr;
+    int rc = plan_enqueue(p, dir, b0, b1, b2, s);   // plain launch first: sets kernel attributes
+    if (rc) return rc;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    rc = plan_enqueue(p, dir, b0, b1, b2, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&p->graph[dir], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    std::memcpy(p->graph_bufs[dir], bufs, sizeof(bufs));
+  }
+  const cudaError_t e = cudaGraphLaunch(p->graph[dir], s);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "graph launch");
+}
+
+}  // namespace
+}  // namespace fds
+
+extern "C" {
+
+int fds_plan_create(const fds_image* images, int32_t n, fds_plan** plan_out) {
+  if (!plan_out) return set_err(FDS_E_INVALID, "null plan pointer");
+  *plan_out = nullptr;
+  int rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((rc = check_descs(images, n))) return rc;
+  }
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  fds_plan* p = new (std::nothrow) fds_plan();
+  if (!p) return set_err(FDS_E_NOMEM, "host allocation failed");
+  p->dev = dev;
+  p->n = n;
+  p->images.assign(images, images + n);
+  p->k_uniform = images[0].k;
+  for (int32_t i = 1; i < n; ++i)
+    if (images[i].k != p->k_uniform) p->k_uniform = -1;
+  const size_t img_bytes = (sizeof(BatchImage) * n + 255) & ~(size_t)255;
+  const size_t ts_bytes = (sizeof(int32_t) * (n + 1) + 255) & ~(size_t)255;
+  cudaError_t e = cudaMalloc(&p->mem, img_bytes + ts_bytes + 256);
+  if (e != cudaSuccess) {
+    delete p;
+    return set_err(FDS_E_NOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  p->d_images = static_cast<BatchImage*>(p->mem);
+  p->d_tile_start = reinterpret_cast<int32_t*>(static_cast<char*>(p->mem) + img_bytes);
+  p->d_dispenser = reinterpret_cast<unsigned int*>(static_cast<char*>(p->mem) + img_bytes + ts_bytes);
+  if ((rc = upload_schedule(p))) {
+    cudaFree(p->mem);
+    delete p;
+    return rc;
+  }
+  *plan_out = p;
+  return FDS_OK;
+}
+
+int fds_plan_destroy(fds_plan* plan) {
+  if (!plan) return FDS_OK;
+  cudaDeviceSynchronize();
+  drop_graphs(plan);
+  cudaFree(plan->mem);
+  delete plan;
+  return FDS_OK;
+}
+
+int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic, int32_t largest_first) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  if (ctas_per_sm != 1 && ctas_per_sm != 2) return set_err(FDS_E_INVALID, "ctas_per_sm must be 1 or 2");
+  int rc = plan_device(plan);
+  if (rc) return rc;
+  plan->per_sm = ctas_per_sm;
+  plan->dynamic = dynamic ? 1 : 0;
+  const int lf = largest_first ? 1 : 0;
+  if (lf != plan->largest_first) {
+    plan->largest_first = lf;
+    cudaError_t e = cudaDeviceSynchronize();   // in-flight launches read the tables
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return upload_schedule(plan);
+  }
+  drop_graphs(plan);
+  return FDS_OK;
+}
+
+int fds_plan_get_schedule(const fds_plan* plan, int32_t* ctas_per_sm, int32_t* dynamic, int32_t* largest_first) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  if (ctas_per_sm) *ctas_per_sm = plan->per_sm;
+  if (dynamic) *dynamic = plan->dynamic;
+  if (largest_first) *largest_first = plan->largest_first;
+  return FDS_OK;
+}
+
+int fds_plan_protect(fds_plan* plan, const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
+                     void* stream) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  int rc = plan_device(plan);
+  if (!rc) rc = plan_buffers_ok(pixels, public_out, private_out);
+  return rc ? rc : plan_enqueue(plan, 0, pixels, public_out, private_out, (cudaStream_t)stream);
+}
+
+int fds_plan_restore(fds_plan* plan, const int16_t* public_in, const uint8_t* private_in,
+                     uint8_t* pixels_out, void* stream) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  int rc = plan_device(plan);
+  if (!rc) rc = plan_buffers_ok(pixels_out, public_in, private_in);
+  return rc ? rc : plan_enqueue(plan, 1, public_in, private_in, pixels_out, (cudaStream_t)stream);
+}
+
+int fds_plan_protect_graph(fds_plan* plan, const uint8_t* pixels, int16_t* public_out,
+                           uint8_t* private_out, void* stream) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  int rc = plan_device(plan);
+  if (!rc) rc = plan_buffers_ok(pixels, public_out, private_out);
+  return rc ? rc : plan_graph(plan, 0, pixels, public_out, private_out, (cudaStream_t)stream);
+}
+
+int fds_plan_restore_graph(fds_plan* plan, const int16_t* public_in, const uint8_t* private_in,
+                           uint8_t* pixels_out, void* stream) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  int rc = plan_device(plan);
+  if (!rc) rc = plan_buffers_ok(pixels_out, public_in, private_in);
+  return rc ? rc : plan_graph(plan, 1, public_in, private_in, pixels_out, (cudaStream_t)stream);
+}
+
+int fds_plan_autotune(fds_plan* plan, const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
+                      int32_t reps, void* stream) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  if (reps < 1) return set_err(FDS_E_INVALID, "reps must be >= 1");
+  int rc = plan_device(plan);
+  if (!rc) rc = plan_buffers_ok(pixels, public_out, private_out);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_err(FDS_E_CUDA, "event creation failed");
+  float best = 1e30f;
+  int32_t bps = 2, bdyn = 0, blf = 0;
+  for (int lf = 0; lf < 2 && !rc; ++lf)
+    for (int dyn = 0; dyn < 2 && !rc; ++dyn)
+      for (int ps = 1; ps <= 2 && !rc; ++ps) {
+        if ((rc = fds_plan_set_schedule(plan, ps, dyn, lf))) break;
+        if ((rc = plan_enqueue(plan, 0, pixels, public_out, private_out, s))) break;   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && !rc; ++r) rc = plan_enqueue(plan, 0, pixels, public_out, private_out, s);
+        cudaEventRecord(e1, s);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          rc = cuda_fail(e, "autotune timing");
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          bps = ps, bdyn = dyn, blf = lf;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  return fds_plan_set_schedule(plan, bps, bdyn, blf);
+}
 
 }  // extern "C"

@@ -1,7 +1,8 @@
 // Fused protect kernel (Sect. 6.3.1, Fig. 6): 8x8 DCT-II per channel, int16 rounding,
 // zigzag fragmentation, AES-128-CTR of the confidential fragment.
 //
-// Persistent CTAs; per tile (see fds_tile.cuh for the decomposition):
+// Persistent CTAs over a tile schedule (one image, or every tile of a batch of images in one
+// launch); per tile (see fds_tile.cuh for the decomposition):
 //   A. the tile's pixels (prefetched with cp.async during the previous tile) are in shared
 //      memory; the previous tile's fragments leave through bulk (TMA engine) stores and the
 //      next tile's pixels start loading
@@ -19,76 +20,87 @@ constexpr int kSmemPix = 0;                                  // 2 pixel tiles
 constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 2 staging areas
 constexpr int kSmemT = kSmemStage + 2 * kCoefBytes;          // AES tables, 4 KB
 constexpr int kSmemQueue = kSmemT + 4096;                    // near-tie queue
-constexpr int kSmemBlk = kSmemQueue + 4 * kQueueCap;         // 2 x 64 block offsets
-constexpr int kSmemMisc = kSmemBlk + 2 * 8 * kTileBlocks;
+constexpr int kSmemSlot = kSmemQueue + 4 * kQueueCap;        // 3 tile slots (ring)
+constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
+constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
 constexpr int kSmemBytes = kSmemMisc + 32;
 
-template <int K, bool DEBUG>
+// the fragments staged for slot sl (buffer st) to global memory; one thread
+__device__ __forceinline__ void store_fragments(const TileSlot* sl, const uint8_t* st) {
+  const int k = sl->k, npub = 63 - k, nb = sl->nb;
+  const int pub_bytes = nb * 6 * npub, priv_bytes = nb * 6 * (k + 1);
+  uint8_t* pdst = sl->pub_out + (uint64_t)sl->local * kTileBlocks * 6ull * npub;
+  uint8_t* vdst = sl->priv_out + (uint64_t)sl->local * kTileBlocks * 6ull * (k + 1);
+  const uint8_t* vsrc = st + kTileCb * 2 * npub;
+  if (pub_bytes >> 4) bulk_store(pdst, st, (uint32_t)(pub_bytes & ~15));
+  if (priv_bytes >> 4) bulk_store(vdst, vsrc, (uint32_t)(priv_bytes & ~15));
+  bulk_commit();
+  for (int j = pub_bytes & ~15; j < pub_bytes; j += 2)
+    *reinterpret_cast<uint16_t*>(pdst + j) = *reinterpret_cast<const uint16_t*>(st + j);
+  for (int j = priv_bytes & ~15; j < priv_bytes; j += 2)
+    *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
+}
+
+// cp.async the pixels of slot sl into pixel tile pix (all threads)
+__device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
+  const uint64_t w3 = (uint64_t)sl->width * 3ull;
+  const int nb = sl->nb;
+  for (int i = threadIdx.x; i < 8 * kTileBlocks * 3; i += kThreads) {
+    const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
+    const int b = rem / 3, q = rem - 3 * b;
+    if (b < nb) cp_async8(pix + y * kRowBytes + b * 24 + 8 * q, sl->px_in + sl->blk[b] + y * w3 + 8 * q);
+  }
+  cp_async_commit();
+}
+
+// BATCH: tiles of many images (round keys from the slot); else one image (round keys read
+// from the kernel parameters, which AES then takes as constant-bank operands)
+template <int K, bool DEBUG, bool BATCH>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
-  uint64_t* blk = reinterpret_cast<uint64_t*>(smem + kSmemBlk);
-  int* misc = reinterpret_cast<int*>(smem + kSmemMisc);  // [0] queue size [1] queued total
-                                                          // [2] escalations [3] failures
-  const int k = K >= 0 ? K : a.k;
-  const int npub = 63 - k;
+  // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
+  int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
   const int t = threadIdx.x;
-  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
-  const uint64_t w3 = (uint64_t)a.width * 3ull;
-  int tile = blockIdx.x;
-  if (tile >= ntiles) return;
+  const int ntiles = a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
+  if ((int)blockIdx.x >= ntiles) return;
+  auto slot = [&](int i) { return reinterpret_cast<TileSlot*>(smem + kSmemSlot + i * kSlotBytes); };
 
   for (int i = t; i < 1024; i += kThreads) Ts[i] = a.T[i];
-  if (t < 8) misc[t] = 0;
-  if (t < kTileBlocks && tile * kTileBlocks + t < a.nblocks) blk[t] = block_offset(a, tile * kTileBlocks + t);
+  if (t < 4) misc[t] = 0;
+  if (t == 0) {
+    misc[4] = next_tile(a, 0);
+    misc[5] = next_tile(a, 1);
+  }
+  if (t < kTileBlocks) fill_slot(a, blockIdx.x, slot(0));
   __syncthreads();
+  load_pixels(slot(0), smem + kSmemPix);
 
-  auto issue_pixels = [&](int tl, int buf) {
-    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
-    uint8_t* pix = smem + kSmemPix + buf * kPixBytes;
-    const uint64_t* bo = blk + buf * kTileBlocks;
-    for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
-      const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
-      const int b = rem / 3, q = rem - 3 * b;
-      if (b < nbl) cp_async8(pix + y * kRowBytes + b * 24 + 8 * q, a.pixels_in + bo[b] + y * w3 + 8 * q);
-    }
-    cp_async_commit();
-  };
-  // the fragments of tile tl, staged in buffer buf, to global memory (one thread)
-  auto issue_store = [&](int tl, int buf) {
-    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
-    const uint8_t* st = smem + kSmemStage + buf * kCoefBytes;
-    const int pub_bytes = nbl * 6 * npub, priv_bytes = nbl * 6 * (k + 1);
-    uint8_t* pdst = reinterpret_cast<uint8_t*>(a.pub_out) + (uint64_t)tl * kTileBlocks * 6ull * npub;
-    uint8_t* vdst = a.priv_out + (uint64_t)tl * kTileBlocks * 6ull * (k + 1);
-    const uint8_t* vsrc = st + kTileCb * 2 * npub;
-    if (pub_bytes >> 4) bulk_store(pdst, st, (uint32_t)(pub_bytes & ~15));
-    if (priv_bytes >> 4) bulk_store(vdst, vsrc, (uint32_t)(priv_bytes & ~15));
-    bulk_commit();
-    for (int j = pub_bytes & ~15; j < pub_bytes; j += 2)
-      *reinterpret_cast<uint16_t*>(pdst + j) = *reinterpret_cast<const uint16_t*>(st + j);
-    for (int j = priv_bytes & ~15; j < priv_bytes; j += 2)
-      *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
-  };
-
-  issue_pixels(tile, 0);
-  int it = 0, prev = -1;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
+  int it = 0;
+  bool have_prev = false;
+  for (;; ++it) {
     const int buf = it & 1;
-    const int next = tile + gridDim.x;
-    const int nb = min(kTileBlocks, a.nblocks - tile * kTileBlocks);
-    if (next < ntiles && t < kTileBlocks && next * kTileBlocks + t < a.nblocks)
-      blk[(buf ^ 1) * kTileBlocks + t] = block_offset(a, next * kTileBlocks + t);
+    // slots: tile it in it % 3, it + 1 in (it + 1) % 3, the one being stored in (it + 2) % 3
+    const int s_cur = it % 3, s_nxt = (it + 1) % 3, s_prev = (it + 2) % 3;
+    const int cur = misc[4 + buf], nxt = misc[4 + (buf ^ 1)];
+    if (cur >= ntiles) break;
+    const TileSlot* sl = slot(s_cur);
+    if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot(s_nxt));
     cp_async_wait_all();
     if (t == 0) {
       if (!DEBUG) bulk_wait_read_all();   // staging[buf] is no longer read by older stores
       misc[0] = 0;
     }
     __syncthreads();                                                       // A
-    if (!DEBUG && t == 0 && prev >= 0) issue_store(prev, buf ^ 1);
-    if (next < ntiles) issue_pixels(next, buf ^ 1);
+    if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
+    if (!DEBUG && t == 0 && have_prev)
+      store_fragments(slot(s_prev), smem + kSmemStage + (buf ^ 1) * kCoefBytes);
+    if (nxt < ntiles) load_pixels(slot(s_nxt), smem + kSmemPix + (buf ^ 1) * kPixBytes);
 
+    const int k = K >= 0 ? K : sl->k;
+    const int npub = 63 - k;
+    const int nb = sl->nb;
     const uint8_t* tile_px = smem + kSmemPix + buf * kPixBytes;
     int16_t* pubst = reinterpret_cast<int16_t*>(smem + kSmemStage + buf * kCoefBytes);
     int16_t* privst = reinterpret_cast<int16_t*>(smem + kSmemStage + buf * kCoefBytes + kTileCb * 2 * npub);
@@ -121,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
         for (int u = 0; u < 8; ++u) f[u][v] = col[u];
       }
       if (DEBUG) {
-        float* out = a.dbg_coefs + ((uint64_t)tile * kTileBlocks * 3 + cb) * 64;
+        float* out = a.dbg_coefs + ((uint64_t)sl->local * kTileBlocks * 3 + cb) * 64;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -187,7 +199,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
         }
       }
     }
-    if (DEBUG) continue;
+    if (DEBUG) {
+      __syncthreads();   // publishes the schedule entry written after barrier A
+      continue;
+    }
     __syncthreads();                                                       // B
     {
       const int nq = min(misc[0], kQueueCap);
@@ -212,14 +227,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
     }
     __syncthreads();                                                       // C
     ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
-             ((uint64_t)tile * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, a, Ts);
+             ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
+             BATCH ? sl->rk : a.rk, Ts);
     fence_proxy_async();
-    prev = tile;
+    have_prev = true;
   }
   if (DEBUG) return;
   __syncthreads();
   if (t == 0) {
-    if (prev >= 0) issue_store(prev, (it - 1) & 1);
+    if (have_prev) store_fragments(slot((it + 2) % 3), smem + kSmemStage + ((it - 1) & 1) * kCoefBytes);
     bulk_wait_all();
     if (a.counters) {
       if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
@@ -229,26 +245,33 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
   }
 }
 
-template <int K, bool DEBUG>
-static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms) {
+template <int K, bool DEBUG, bool BATCH>
+static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(protect_kernel<K, DEBUG>,
+    cudaError_t e = cudaFuncSetAttribute(protect_kernel<K, DEBUG, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
-  const int grid = ntiles < kCtasPerSm * sms ? ntiles : kCtasPerSm * sms;
-  protect_kernel<K, DEBUG><<<grid, kThreads, kSmemBytes, s>>>(a);
+  const int ntiles = total_tiles(a);
+  const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
+  const int grid = ntiles < cap ? ntiles : cap;
+  if (grid > 0) protect_kernel<K, DEBUG, BATCH><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms) {
-  if (debug) return launch_k<-1, true>(a, s, sms);
-  if (a.k == 0) return launch_k<0, false>(a, s, sms);
-  if (a.k == 5) return launch_k<5, false>(a, s, sms);
-  return launch_k<-1, false>(a, s, sms);
+// k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile
+cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm) {
+  if (debug) return launch_k<-1, true, false>(a, s, sms, per_sm);
+  if (a.images) {
+    if (a.k == 0) return launch_k<0, false, true>(a, s, sms, per_sm);
+    if (a.k == 5) return launch_k<5, false, true>(a, s, sms, per_sm);
+    return launch_k<-1, false, true>(a, s, sms, per_sm);
+  }
+  if (a.k == 0) return launch_k<0, false, false>(a, s, sms, per_sm);
+  if (a.k == 5) return launch_k<5, false, false>(a, s, sms, per_sm);
+  return launch_k<-1, false, false>(a, s, sms, per_sm);
 }
 
 }  // namespace fds

@@ -2,7 +2,8 @@
 // decryption of the confidential fragment, merge with the public fragment by zigzag
 // position, inverse 8x8 DCT, round half away from zero (exact), clamp to [0, 255].
 //
-// Persistent CTAs; per tile (see fds_tile.cuh for the decomposition):
+// Persistent CTAs over a tile schedule (one image, or every tile of a batch of images in one
+// launch); per tile (see fds_tile.cuh for the decomposition):
 //   A. the tile's fragments are in shared memory, already decrypted; the next tile's start
 //      loading (cp.async)
 //   1. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
@@ -18,8 +19,9 @@ namespace fds {
 constexpr int kSmemCoef = 0;                                 // 2 fragment staging areas
 constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 1 pixel tile
 constexpr int kSmemQueue = kSmemPix + kPixBytes;
-constexpr int kSmemBlk = kSmemQueue + 4 * kQueueCap;
-constexpr int kSmemMisc = kSmemBlk + 8 * kTileBlocks;
+constexpr int kSmemSlot = kSmemQueue + 4 * kQueueCap;        // 3 tile slots (ring)
+constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
+constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
 constexpr int kSmemBytes = kSmemMisc + 32;
 
 // gather the 64 int16 coefficients of tile channel-block cb in zigzag order, two per word
@@ -35,73 +37,81 @@ __device__ __forceinline__ void gather_coefs(const int16_t* pubst, const int16_t
   }
 }
 
-template <int K>
+// cp.async the public and private ranges of slot sl's tile into staging area st
+__device__ __forceinline__ void load_fragments(const TileSlot* sl, uint8_t* st) {
+  const int t = threadIdx.x;
+  const int k = sl->k, npub = 63 - k, nb = sl->nb;
+  const int pub_bytes = nb * 6 * npub, priv_bytes = nb * 6 * (k + 1);
+  const uint8_t* psrc = sl->pub_in + (uint64_t)sl->local * kTileBlocks * 6ull * npub;
+  const uint8_t* vsrc = sl->priv_in + (uint64_t)sl->local * kTileBlocks * 6ull * (k + 1);
+  uint8_t* vdst = st + kTileCb * 2 * npub;
+  const int p16 = pub_bytes >> 4, v16 = priv_bytes >> 4;
+  for (int i = t; i < p16 + v16; i += kThreads) {
+    if (i < p16)
+      cp_async16(st + 16 * i, psrc + 16 * i);
+    else
+      cp_async16(vdst + 16 * (i - p16), vsrc + 16 * (i - p16));
+  }
+  for (int j = (p16 << 4) + 2 * t; j < pub_bytes; j += 2 * kThreads)
+    *reinterpret_cast<uint16_t*>(st + j) = *reinterpret_cast<const uint16_t*>(psrc + j);
+  for (int j = (v16 << 4) + 2 * t; j < priv_bytes; j += 2 * kThreads)
+    *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
+  cp_async_commit();
+}
+
+// CTR decryption of the private range of slot sl's tile, in staging area st
+__device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint32_t* rk, uint8_t* st,
+                                                  const uint32_t* Ts) {
+  const int k = sl->k;
+  ctr_tile(st + kTileCb * 2 * (63 - k), sl->nb * 6 * (k + 1),
+           ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl, rk, Ts);
+}
+
+// BATCH: tiles of many images (round keys from the slot); else one image (round keys read
+// from the kernel parameters, which AES then takes as constant-bank operands)
+template <int K, bool BATCH>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) uint32_t Ts[1024];                // AES T-tables
   uint8_t* pix = smem + kSmemPix;
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
-  uint64_t* blk = reinterpret_cast<uint64_t*>(smem + kSmemBlk);
+  // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
-
-  const int k = K >= 0 ? K : a.k;
-  const int npub = 63 - k;
   const int t = threadIdx.x;
-  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
-  const uint64_t w3 = (uint64_t)a.width * 3ull;
-  int tile = blockIdx.x;
-  if (tile >= ntiles) return;
+  const int ntiles = a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
+  if ((int)blockIdx.x >= ntiles) return;
+  auto slot = [&](int i) { return reinterpret_cast<TileSlot*>(smem + kSmemSlot + i * kSlotBytes); };
+  auto stage = [&](int i) { return smem + kSmemCoef + i * kCoefBytes; };
 
   for (int i = t; i < 1024; i += kThreads) Ts[i] = a.T[i];
-  if (t < 8) misc[t] = 0;
-
-  // cp.async the tile's public and private ranges into staging buffer buf
-  auto issue_frag = [&](int tl, int buf) {
-    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
-    uint8_t* st = smem + kSmemCoef + buf * kCoefBytes;
-    const int pub_bytes = nbl * 6 * npub, priv_bytes = nbl * 6 * (k + 1);
-    const uint8_t* psrc = reinterpret_cast<const uint8_t*>(a.pub_in) + (uint64_t)tl * kTileBlocks * 6ull * npub;
-    const uint8_t* vsrc = a.priv_in + (uint64_t)tl * kTileBlocks * 6ull * (k + 1);
-    uint8_t* vdst = st + kTileCb * 2 * npub;
-    const int p16 = pub_bytes >> 4, v16 = priv_bytes >> 4;
-    for (int i = t; i < p16 + v16; i += kThreads) {
-      if (i < p16)
-        cp_async16(st + 16 * i, psrc + 16 * i);
-      else
-        cp_async16(vdst + 16 * (i - p16), vsrc + 16 * (i - p16));
-    }
-    for (int j = (p16 << 4) + 2 * t; j < pub_bytes; j += 2 * kThreads)
-      *reinterpret_cast<uint16_t*>(st + j) = *reinterpret_cast<const uint16_t*>(psrc + j);
-    for (int j = (v16 << 4) + 2 * t; j < priv_bytes; j += 2 * kThreads)
-      *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
-    cp_async_commit();
-  };
-
-  auto decrypt = [&](int tl, int buf) {
-    const int nbl = min(kTileBlocks, a.nblocks - tl * kTileBlocks);
-    uint8_t* vst = smem + kSmemCoef + buf * kCoefBytes + kTileCb * 2 * npub;
-    ctr_tile(vst, nbl * 6 * (k + 1), ((uint64_t)tl * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, a, Ts);
-  };
-
-  issue_frag(tile, 0);
+  if (t < 4) misc[t] = 0;
+  if (t == 0) {
+    misc[4] = next_tile(a, 0);
+    misc[5] = next_tile(a, 1);
+  }
+  if (t < kTileBlocks) fill_slot(a, blockIdx.x, slot(0));
+  __syncthreads();
+  load_fragments(slot(0), stage(0));
   cp_async_wait_all();
   __syncthreads();
-  decrypt(tile, 0);
-  int it = 0;
+  decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
   int esc = 0;
   bool fail = false;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
+  for (int it = 0;; ++it) {
     const int buf = it & 1;
-    const int next = tile + gridDim.x;
-    const int nb = min(kTileBlocks, a.nblocks - tile * kTileBlocks);
+    const int cur = misc[4 + buf], nxt = misc[4 + (buf ^ 1)];
+    if (cur >= ntiles) break;
+    const TileSlot* sl = slot(it % 3);
+    if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot((it + 1) % 3));
     if (t == 0) misc[0] = 0;
     __syncthreads();                                                       // A
-    if (next < ntiles) issue_frag(next, buf ^ 1);
-    if (t < nb) blk[t] = block_offset(a, tile * kTileBlocks + t);
-    const uint8_t* st = smem + kSmemCoef + buf * kCoefBytes;
-    const int16_t* pubst = reinterpret_cast<const int16_t*>(st);
-    const int16_t* privst = reinterpret_cast<const int16_t*>(st + kTileCb * 2 * npub);
-
+    if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
+    if (nxt < ntiles) load_fragments(slot((it + 1) % 3), stage(buf ^ 1));
+    const int k = K >= 0 ? K : sl->k;
+    const int npub = 63 - k;
+    const int nb = sl->nb;
+    const int16_t* pubst = reinterpret_cast<const int16_t*>(stage(buf));
+    const int16_t* privst = reinterpret_cast<const int16_t*>(stage(buf) + kTileCb * 2 * npub);
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
     if (b < nb) {
       const int16_t* pub_cb = pubst + cb * npub;
@@ -180,14 +190,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       if (t == 0) misc[1] += misc[0];
     }
     __syncthreads();                                                       // C
-    for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
-      const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
-      const int bb = rem / 3, q = rem - 3 * bb;
-      if (bb < nb)
-        *reinterpret_cast<uint2*>(a.pixels_out + blk[bb] + y * w3 + 8 * q) =
-            *reinterpret_cast<const uint2*>(pix + y * kRowBytes + bb * 24 + 8 * q);
+    {
+      const uint64_t w3 = (uint64_t)sl->width * 3ull;
+      for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
+        const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
+        const int bb = rem / 3, q = rem - 3 * bb;
+        if (bb < nb)
+          *reinterpret_cast<uint2*>(sl->px_out + sl->blk[bb] + y * w3 + 8 * q) =
+              *reinterpret_cast<const uint2*>(pix + y * kRowBytes + bb * 24 + 8 * q);
+      }
     }
-    if (next < ntiles) decrypt(next, buf ^ 1);
+    if (nxt < ntiles) decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
   }
   if (esc) atomicAdd(&misc[2], esc);
   if (fail) atomicAdd(&misc[3], 1);
@@ -199,25 +212,32 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
   }
 }
 
-template <int K>
-static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms) {
+template <int K, bool BATCH>
+static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(restore_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(restore_kernel<K, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int ntiles = (a.nblocks + kTileBlocks - 1) / kTileBlocks;
-  const int grid = ntiles < kCtasPerSm * sms ? ntiles : kCtasPerSm * sms;
-  restore_kernel<K><<<grid, kThreads, kSmemBytes, s>>>(a);
+  const int ntiles = total_tiles(a);
+  const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
+  const int grid = ntiles < cap ? ntiles : cap;
+  if (grid > 0) restore_kernel<K, BATCH><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms) {
-  if (a.k == 0) return launch_k<0>(a, s, sms);
-  if (a.k == 5) return launch_k<5>(a, s, sms);
-  return launch_k<-1>(a, s, sms);
+// k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile
+cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
+  if (a.images) {
+    if (a.k == 0) return launch_k<0, true>(a, s, sms, per_sm);
+    if (a.k == 5) return launch_k<5, true>(a, s, sms, per_sm);
+    return launch_k<-1, true>(a, s, sms, per_sm);
+  }
+  if (a.k == 0) return launch_k<0, false>(a, s, sms, per_sm);
+  if (a.k == 5) return launch_k<5, false>(a, s, sms, per_sm);
+  return launch_k<-1, false>(a, s, sms, per_sm);
 }
 
 }  // namespace fds

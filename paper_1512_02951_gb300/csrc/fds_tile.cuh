@@ -34,6 +34,16 @@ constexpr float kGuardFwd = 1.0f / 512.0f;
 // Inverse guard per channel-block: error <= 2.89 u sum|F| (u = 2^-24); 2^-22 sum|F| is used.
 constexpr float kGuardInvScale = 1.0f / 4194304.0f;
 
+// One image of a batch as the kernels read it (device copy of struct fds_image).
+struct BatchImage {
+  uint64_t pixel_offset, public_offset, private_offset;
+  int32_t width, height, k, key_slot;
+  uint64_t iv_hi, iv_lo;
+};
+
+// Kernel arguments.  Single image: `images` is null and the image fields describe it.
+// Batch: the pointers are the batch buffers, images[i] gives each image's offsets, and
+// global tile g belongs to the image i with tile_start[i] <= g < tile_start[i + 1].
 struct TileArgs {
   const uint8_t* pixels_in;
   uint8_t* pixels_out;
@@ -49,11 +59,36 @@ struct TileArgs {
   int32_t width, bx_count, nblocks, k;
   uint64_t iv_hi, iv_lo;          // initial counter block, big-endian halves
   uint32_t rk[44];                // AES-128 round keys
+  // batch mode
+  const BatchImage* images;       // device, n_images entries; null for a single image
+  const int32_t* tile_start;      // device, n_images + 1 prefix sums of tiles per image
+  const uint32_t* round_keys;     // device, FDS_MAX_KEYS x 44 words
+  unsigned int* dispenser;        // device tile counter (dynamic dispatch), or null (static)
+  int32_t n_images, total_tiles;
 };
 
-// launchers (one translation unit each); `sms` = number of SMs of the device
-cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms);
-cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms);
+// What a CTA knows about the tile it is working on (shared memory, filled one tile ahead).
+struct TileSlot {
+  uint64_t blk[kTileBlocks];      // byte offset of each block's top-left pixel in the image
+  uint32_t rk[44];                // the image's AES-128 round keys
+  const uint8_t* px_in;           // the image's pixels, public and private fragments
+  uint8_t* px_out;
+  const uint8_t* pub_in;
+  uint8_t* pub_out;
+  const uint8_t* priv_in;
+  uint8_t* priv_out;
+  uint64_t iv_hi, iv_lo;
+  int32_t width, k, local, nb;    // local = tile index inside the image; nb = its blocks
+};
+
+// launchers (one translation unit each); `sms` = number of SMs of the device, `per_sm` =
+// resident CTAs per SM to launch (1 or 2)
+cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 2);
+cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 2);
+
+inline int total_tiles(const TileArgs& a) {
+  return a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -84,9 +119,64 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 
 // byte offset of block gb's top-left pixel in an H x W x 3 image
-__device__ __forceinline__ uint64_t block_offset(const TileArgs& a, int gb) {
-  const int by = gb / a.bx_count, bx = gb - by * a.bx_count;
-  return (uint64_t)by * 8ull * (uint64_t)a.width * 3ull + (uint64_t)bx * 24ull;
+__device__ __forceinline__ uint64_t block_offset(int width, int gb) {
+  const int bxc = width >> 3;
+  const int by = gb / bxc, bx = gb - by * bxc;
+  return (uint64_t)by * 8ull * (uint64_t)width * 3ull + (uint64_t)bx * 24ull;
+}
+
+// Fill slot s for global tile g.  Called by threads 0 .. kTileBlocks-1 of the CTA (each
+// writes its own fields); the caller publishes the slot with a barrier.
+__device__ __forceinline__ void fill_slot(const TileArgs& a, int g, TileSlot* s) {
+  const int t = threadIdx.x;
+  int width, nblocks, k, local;
+  uint64_t iv_hi, iv_lo, pxo = 0, puo = 0, pro = 0;
+  const uint32_t* rk;
+  if (a.images == nullptr) {
+    width = a.width, nblocks = a.nblocks, k = a.k, local = g;
+    iv_hi = a.iv_hi, iv_lo = a.iv_lo;
+    rk = a.rk;
+  } else {
+    int lo = 0, hi = a.n_images;                 // tile_start[lo] <= g < tile_start[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(a.tile_start + mid) <= g)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const BatchImage& im = a.images[lo];
+    width = im.width, k = im.k, local = g - __ldg(a.tile_start + lo);
+    nblocks = (im.width >> 3) * (im.height >> 3);
+    iv_hi = im.iv_hi, iv_lo = im.iv_lo;
+    pxo = im.pixel_offset, puo = im.public_offset, pro = im.private_offset;
+    rk = a.round_keys + 44 * im.key_slot;
+  }
+  const int nb = min(kTileBlocks, nblocks - local * kTileBlocks);
+  if (t == 0) {
+    s->px_in = a.pixels_in + pxo;
+    s->px_out = a.pixels_out + pxo;
+    s->pub_in = reinterpret_cast<const uint8_t*>(a.pub_in) + puo;
+    s->pub_out = reinterpret_cast<uint8_t*>(a.pub_out) + puo;
+    s->priv_in = a.priv_in + pro;
+    s->priv_out = a.priv_out + pro;
+    s->iv_hi = iv_hi;
+    s->iv_lo = iv_lo;
+    s->width = width;
+    s->k = k;
+    s->local = local;
+    s->nb = nb;
+  }
+  if (t < 44) s->rk[t] = rk[t];
+  if (t < nb) s->blk[t] = block_offset(width, local * kTileBlocks + t);
+}
+
+// Tile schedule of a persistent CTA: the i-th tile is blockIdx.x + i * gridDim.x (static), or
+// for i >= 1 the value of an atomic counter plus gridDim.x (dynamic, a.dispenser non-null;
+// the counter must be zero at launch).  Called by one thread.
+__device__ __forceinline__ int next_tile(const TileArgs& a, int i) {
+  if (a.dispenser == nullptr || i == 0) return blockIdx.x + i * gridDim.x;
+  return (int)atomicAdd(a.dispenser, 1u) + (int)gridDim.x;
 }
 
 // 24-byte block row of the pixel tile shifted right by `c` bytes: channel c's pixel x is
@@ -102,13 +192,14 @@ __device__ __forceinline__ void load_row_shifted(const uint8_t* tile, int y, int
 
 // AES-128-CTR over `bytes` bytes of a 16-byte aligned staging area whose first byte is byte
 // 16 * first_block of the image's private message.
+// The IV comes from the tile's slot; rk are the 44 round keys.
 __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_block,
-                                         const TileArgs& a, const uint32_t* Ts) {
+                                         const TileSlot* sl, const uint32_t* rk, const uint32_t* Ts) {
   const int nblk = (bytes + 15) >> 4;
   for (int i = threadIdx.x; i < nblk; i += kThreads) {
     uint32_t s[4];
-    ctr_block(a.iv_hi, a.iv_lo, first_block + i, s);
-    aes128_encrypt(s, a.rk, Ts);
+    ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s);
+    aes128_encrypt(s, rk, Ts);
     uint4* p = reinterpret_cast<uint4*>(st + 16 * i);
     uint4 d = *p;
     d.x ^= s[0];

@@ -99,3 +99,19 @@ def test_generated_header_is_up_to_date():
     out = subprocess.run([sys.executable, os.path.join(csrc, "gen_cos_limbs.py")],
                          capture_output=True, text=True, check=True).stdout
     assert out == open(os.path.join(csrc, "fds_cos_limbs.h")).read()
+
+
+def test_plan_arguments_are_checked_on_the_host(lib):
+    from paper_1512_02951_gb300 import _lib
+
+    h = ctypes.c_void_p()
+    assert lib.fds_plan_create(None, 0, ctypes.byref(h)) == -1
+    d = (_lib.FdsImage * 1)()
+    d[0].width, d[0].height, d[0].k, d[0].key_slot = 60, 64, 0, 0
+    assert lib.fds_plan_create(d, 1, ctypes.byref(h)) == -1                 # width % 8
+    d[0].width, d[0].key_slot = 64, 7
+    assert lib.fds_plan_create(d, 1, ctypes.byref(h)) == -2                 # slot not registered
+    d[0].key_slot, d[0].public_offset = 0, 8
+    assert lib.fds_plan_create(d, 1, ctypes.byref(h)) in (-1, -2)           # misaligned offset
+    assert lib.fds_plan_set_schedule(None, 1, 0, 0) == -1
+    assert lib.fds_plan_destroy(None) == 0
