@@ -160,6 +160,33 @@ int fds_plan_protect_graph(fds_plan* plan, const uint8_t* pixels, int16_t* publi
 int fds_plan_restore_graph(fds_plan* plan, const int16_t* public_in, const uint8_t* private_in,
                            uint8_t* pixels_out, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batch protect that allocates nothing (the paper has no counterpart; this is an interface
+ * convenience of this library).
+ *
+ * Some callers cannot allocate device memory at the point where they protect a batch: a
+ * host framework that owns all device memory through its own pool and forbids allocations
+ * behind its back, a latency-critical loop in which cudaMalloc / cudaFree would synchronise
+ * the device, or an embedded service that must not fail at run time for lack of memory.
+ * fds_protect_batch_noalloc gives them the same one-launch batched protect as
+ * fds_plan_protect (same outputs, bit for bit) without a plan: the batch's descriptor
+ * table, tile prefix sums and tile counter live in one fixed scratch area that the library
+ * holds in static device memory (about 214 KB, kept on every GPU that loads the library
+ * until the process exits).
+ *
+ * - n must be 1 .. FDS_NOALLOC_MAX_IMAGES, else FDS_E_INVALID; buffers, offsets and keys as
+ *   for fds_protect.  The caller allocates pixels, public_out and private_out.
+ * - The first call on a device looks up the scratch area's device address (once per
+ *   device, with that device current); make that first call before any stream capture.
+ * - Every call reuses the same scratch area and overwrites it on `stream`: calls that can
+ *   overlap on the GPU (other streams, other host threads) race and must be serialised by
+ *   the caller.
+ * - It calls no cudaMalloc, cudaFree or other allocating CUDA routine.
+ */
+#define FDS_NOALLOC_MAX_IMAGES 4096
+int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
+                              const fds_image* images, int32_t n, void* stream);
+
 /* Diagnostics: the float32 coefficients the protect kernel computes before rounding, as
  * float [H/8][W/8][3][8][8] ([u][v] inside a block).  coefs_out: device.  Used to compare
  * the pre-rounding values with a float64 reference (Sect. 6.4.3 precision concern). */

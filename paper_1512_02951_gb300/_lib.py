@@ -15,6 +15,7 @@ FDS_E_CUDA = -4
 FDS_E_TIMEOUT = -5
 FDS_E_BUSY = -6
 FDS_MAX_KEYS = 256
+FDS_NOALLOC_MAX_IMAGES = 4096
 
 _c_u8p = ctypes.POINTER(ctypes.c_uint8)
 
@@ -64,6 +65,9 @@ SIGNATURES = {
     "fds_plan_restore": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "fds_plan_protect_graph": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "fds_plan_restore_graph": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "fds_protect_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.POINTER(FdsImage), ctypes.c_int32,
+                                                 ctypes.c_void_p]),
     "fds_debug_dct_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "fds_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),

@@ -219,3 +219,15 @@ class Plan:
         fn = _lib.load().fds_plan_restore_graph if graph else _lib.load().fds_plan_restore
         _lib.check(fn(self._h, public.data_ptr(), private.data_ptr(), pixels_out.data_ptr(),
                       _stream_ptr(pixels_out.device)), "fds_plan_restore")
+
+
+def protect_batch_noalloc(pixels: torch.Tensor, public_out: torch.Tensor,
+                          private_out: torch.Tensor, descs: Sequence[ImageDesc]) -> None:
+    """fds_protect_batch_noalloc: the one-launch batched protect for callers that cannot
+    allocate device memory; the library allocates nothing (its scratch is static device
+    memory shared by all calls, so calls that overlap on the GPU must be serialised)."""
+    arr = _desc_array(descs)
+    rc = _lib.load().fds_protect_batch_noalloc(pixels.data_ptr(), public_out.data_ptr(),
+                                               private_out.data_ptr(), arr, len(descs),
+                                               _stream_ptr(pixels.device))
+    _lib.check(rc, "fds_protect_batch_noalloc")

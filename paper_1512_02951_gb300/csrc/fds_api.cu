@@ -707,3 +707,97 @@ int fds_plan_autotune(fds_plan* plan, const uint8_t* pixels, int16_t* public_out
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// batch protect without allocation: the batch's descriptor table, tile prefix sums and tile
+// counter live in a fixed static device array instead of plan memory
+namespace fds {
+
+constexpr size_t kNoAllocImgBytes = sizeof(BatchImage) * FDS_NOALLOC_MAX_IMAGES;
+constexpr size_t kNoAllocTsBytes = ((sizeof(int32_t) * (FDS_NOALLOC_MAX_IMAGES + 1)) + 255) & ~(size_t)255;
+constexpr size_t kNoAllocBytes = kNoAllocImgBytes + kNoAllocTsBytes + 256;
+
+// the scratch area; every call overwrites it (see fds.h)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+unsigned char* g_noalloc_addr[kMaxDevices];   // device address of the scratch, per device
+constexpr int kNoAllocChunk = 128;            // descriptors staged per host->device copy
+}  // namespace
+
+}  // namespace fds
+
+extern "C" int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
+                                         const fds_image* images, int32_t n, void* stream) {
+  if (n < 1 || n > FDS_NOALLOC_MAX_IMAGES)
+    return set_err(FDS_E_INVALID, "fds_protect_batch_noalloc takes 1 to " +
+                                      std::to_string(FDS_NOALLOC_MAX_IMAGES) + " images, got " +
+                                      std::to_string(n));
+  int rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((rc = check_descs(images, n))) return rc;
+  }
+  if ((rc = plan_buffers_ok(pixels, public_out, private_out))) return rc;
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  unsigned char* base;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_noalloc_addr[dev]) {   // once per device, with that device current
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "scratch address");
+      g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchImage* d_img = reinterpret_cast<BatchImage*>(base);
+  int32_t* d_ts = reinterpret_cast<int32_t*>(base + kNoAllocImgBytes);
+  unsigned int* d_counter = reinterpret_cast<unsigned int*>(base + kNoAllocImgBytes + kNoAllocTsBytes);
+  // descriptors and tile prefix sums, staged through small host buffers on the stack
+  BatchImage bi[kNoAllocChunk];
+  int32_t ts[kNoAllocChunk + 1];
+  int64_t acc = 0;
+  int32_t k_uniform = images[0].k;
+  for (int32_t c0 = 0; c0 < n; c0 += kNoAllocChunk) {
+    const int32_t m = std::min<int32_t>(kNoAllocChunk, n - c0);
+    for (int32_t j = 0; j < m; ++j) {
+      const fds_image& d = images[c0 + j];
+      BatchImage& b = bi[j];
+      b.pixel_offset = d.pixel_offset;
+      b.public_offset = d.public_offset;
+      b.private_offset = d.private_offset;
+      b.width = d.width;
+      b.height = d.height;
+      b.k = d.k;
+      b.key_slot = d.key_slot;
+      iv_words(d.iv, &b.iv_hi, &b.iv_lo);
+      if (d.k != k_uniform) k_uniform = -1;
+      ts[j] = (int32_t)acc;
+      acc += ((int64_t)(d.width / 8) * (d.height / 8) + kTileBlocks - 1) / kTileBlocks;
+      if (acc > (1ll << 30)) return set_err(FDS_E_INVALID, "batch too large");
+    }
+    const int32_t extra = (c0 + m == n) ? 1 : 0;   // the last chunk also writes tile_start[n]
+    if (extra) ts[m] = (int32_t)acc;
+    // pageable source: the copy has consumed the stack buffer when the call returns
+    cudaError_t e = cudaMemcpyAsync(d_img + c0, bi, sizeof(BatchImage) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_ts + c0, ts, sizeof(int32_t) * (m + extra), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch upload");
+  }
+  const cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s);   // must start at 0
+  if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+  TileArgs a{};
+  a.pixels_in = pixels;
+  a.pub_out = public_out;
+  a.priv_out = private_out;
+  a.images = d_img;
+  a.tile_start = d_ts;
+  a.n_images = n;
+  a.total_tiles = (int32_t)acc;
+  a.k = k_uniform;
+  a.dispenser = d_counter;
+  return run_protect(a, dev, s, false, 2);
+}
