@@ -464,9 +464,73 @@ def batch_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------
+# serving form: Poisson arrivals, mixed protect / restore, continuous batching
+SERVE_N, SERVE_RATE, SERVE_SEED = 1500, 500.0, 4242
+
+
+def serve_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_1512_02951_gb300 import api, build, synth
+    from paper_1512_02951_gb300.serve import Request, Server, run_poisson
+
+    build.build()
+    api.init(0)
+    sizes, crops = batch_inputs(SERVE_N, SERVE_SEED)
+    keys = [synth.make_key(SERVE_SEED + 100 + i) for i in range(64)]
+    slots = [api.key_register(k) for k in keys]
+    rng = np.random.default_rng(SERVE_SEED)
+
+    def make_requests():
+        reqs = []
+        for i, (b, y0, x0, w, h) in enumerate(crops):
+            img = torch.from_numpy(np.ascontiguousarray(b[y0: y0 + h, x0: x0 + w])).pin_memory()
+            slot = slots[int(rng.integers(0, 64))]
+            iv = synth.make_iv(SERVE_SEED + 1000 + i)
+            if i % 2 == 0:
+                reqs.append(Request("protect", w, h, 0, slot, iv, pixels=img))
+            else:                                   # restore inputs, protected beforehand
+                pub, priv = api.protect_image(img.cuda(), keys[slots.index(slot)], iv, 0)
+                reqs.append(Request("restore", w, h, 0, slot, iv, public=pub.cpu().pin_memory(),
+                                    private=priv.cpu().pin_memory()))
+        torch.cuda.synchronize()
+        return reqs
+
+    reqs = make_requests()
+    arrivals = synth.poisson_arrivals(len(reqs), SERVE_RATE, SERVE_SEED)
+    srv = Server(lanes=3, max_batch=64)
+    warm = [Request(r.kind, r.width, r.height, r.k, r.key_slot, r.iv, r.pixels, r.public, r.private)
+            for r in reqs[:32]]
+    run_poisson(srv, warm, np.zeros(len(warm)))
+    poisson = run_poisson(srv, reqs, arrivals)
+    stats_p = dict(srv.stats)
+    again = [Request(r.kind, r.width, r.height, r.k, r.key_slot, r.iv, r.pixels, r.public, r.private)
+             for r in reqs]
+    burst = run_poisson(srv, again, np.zeros(len(again)))      # all at once: saturation
+    srv.close()
+    same = all((np.array_equal(a.future.result()[0], b.future.result()[0]) and
+                a.future.result()[1] == b.future.result()[1]) if a.kind == "protect"
+               else np.array_equal(a.future.result(), b.future.result()) for a, b in zip(reqs, again))
+    line = {"metric": "serving p50/p99 ms per request and sustained MB/s of pixels",
+            "value": round(poisson["p99_ms"], 3), "unit": "ms (p99)", "n_gpus": 1,
+            "steps": len(reqs), "warmup": len(warm), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{SERVE_N} requests, Poisson {SERVE_RATE:g} req/s, 50/50 protect/restore, "
+                                   "W,H log-uniform [64,2048], k=0, 64 device-resident keys, "
+                                   "memory-based admission, 3 lanes, batches up to 64"},
+            "poisson": {k: round(v, 3) for k, v in poisson.items()},
+            "saturation": {k: round(v, 3) for k, v in burst.items()},
+            "batches": stats_p["batches"], "max_batch": stats_p["max_batch"],
+            "max_lanes_busy": stats_p["max_lanes_busy"],
+            "same_results_in_both_runs": same}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["image4096", "batch2000"], default="image4096")
+    ap.add_argument("--workload", choices=["image4096", "batch2000", "serve"], default="image4096")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
@@ -485,6 +549,8 @@ def main():
         reference_arm(args)
     elif args.workload == "batch2000":
         batch_arm(args)
+    elif args.workload == "serve":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

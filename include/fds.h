@@ -129,6 +129,15 @@ int fds_plan_create(const fds_image* images, int32_t n, fds_plan** plan_out);
 /* Free a plan (synchronises the device first). */
 int fds_plan_destroy(fds_plan* plan);
 
+/* Create an empty, reusable plan with room for `capacity` images (device tables plus pinned
+ * host staging).  Fill it with fds_plan_update; launching an empty plan does nothing. */
+int fds_plan_reserve(int32_t capacity, fds_plan** plan_out);
+
+/* Replace the plan's batch with n <= capacity images.  The tables are copied
+ * asynchronously on `stream`: launches of this plan must be on the same stream (or ordered
+ * after it).  Waits only for the previous update's copy to have left the staging area. */
+int fds_plan_update(fds_plan* plan, const fds_image* images, int32_t n, void* stream);
+
 /* Schedule of the persistent launch.  ctas_per_sm: 1 or 2 resident CTAs per SM;
  * dynamic: 0 = static round-robin tile assignment, 1 = tiles handed out by an atomic
  * counter; largest_first: 0 = tiles in descriptor order, 1 = images by decreasing size.

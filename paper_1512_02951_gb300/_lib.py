@@ -54,6 +54,9 @@ SIGNATURES = {
     "fds_plan_create": (ctypes.c_int, [ctypes.POINTER(FdsImage), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "fds_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fds_plan_reserve": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "fds_plan_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(FdsImage), ctypes.c_int32,
+                                       ctypes.c_void_p]),
     "fds_plan_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_int32]),
     "fds_plan_get_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),

@@ -175,11 +175,24 @@ class Plan:
     """fds_plan_*: a batch whose descriptors and tile schedule live on the device, run as one
     persistent launch (optionally through a CUDA graph)."""
 
-    def __init__(self, descs: Sequence[ImageDesc]):
-        arr = _desc_array(descs)
+    def __init__(self, descs: Sequence[ImageDesc] | None = None, capacity: int = 0):
+        """A plan for `descs`, or (descs None) an empty reusable plan for `capacity` images."""
         h = ctypes.c_void_p()
-        _lib.check(_lib.load().fds_plan_create(arr, len(descs), ctypes.byref(h)), "fds_plan_create")
+        if descs is None:
+            _lib.check(_lib.load().fds_plan_reserve(capacity, ctypes.byref(h)), "fds_plan_reserve")
+            self.descs = []
+        else:
+            arr = _desc_array(descs)
+            _lib.check(_lib.load().fds_plan_create(arr, len(descs), ctypes.byref(h)),
+                       "fds_plan_create")
+            self.descs = list(descs)
         self._h = h
+
+    def update(self, descs: Sequence[ImageDesc], stream: torch.cuda.Stream | None = None) -> None:
+        """fds_plan_update: replace the batch of a reusable plan (copies on `stream`)."""
+        arr = _desc_array(descs)
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _lib.check(_lib.load().fds_plan_update(self._h, arr, len(descs), s), "fds_plan_update")
         self.descs = list(descs)
 
     def close(self) -> None:

@@ -416,9 +416,11 @@ const char* fds_last_error(void) { return t_err.c_str(); }
 struct fds_plan {
   int dev = 0;
   std::vector<fds_image> images;        // host copy, caller's order
-  int32_t n = 0, total_tiles = 0, k_uniform = -1;
+  int32_t n = 0, total_tiles = 0, k_uniform = -1, capacity = 0;
   int32_t per_sm = 2, dynamic = 0, largest_first = 0;
-  void* mem = nullptr;                  // device: BatchImage[n], tile_start[n+1], counter
+  void* mem = nullptr;                  // device: BatchImage[cap], tile_start[cap+1], counter
+  void* host = nullptr;                 // pinned staging of reusable plans (fds_plan_reserve)
+  cudaEvent_t staged = nullptr;         // the last asynchronous update has left `host`
   fds::BatchImage* d_images = nullptr;
   int32_t* d_tile_start = nullptr;
   unsigned int* d_dispenser = nullptr;
@@ -451,16 +453,14 @@ void drop_graphs(fds_plan* p) {
   }
 }
 
-// device tables of the plan in its current order
-int upload_schedule(fds_plan* p) {
+// the plan's tables in its current order, into host arrays bi[n] and ts[n + 1]
+int build_tables(fds_plan* p, BatchImage* bi, int32_t* ts) {
   std::vector<int> order(p->n);
   for (int i = 0; i < p->n; ++i) order[i] = i;
   if (p->largest_first)
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
       return (int64_t)p->images[x].width * p->images[x].height > (int64_t)p->images[y].width * p->images[y].height;
     });
-  std::vector<BatchImage> bi(p->n);
-  std::vector<int32_t> ts(p->n + 1);
   int64_t acc = 0;
   for (int j = 0; j < p->n; ++j) {
     const fds_image& d = p->images[order[j]];
@@ -479,7 +479,22 @@ int upload_schedule(fds_plan* p) {
   if (acc > (1ll << 30)) return set_err(FDS_E_INVALID, "batch too large");
   ts[p->n] = (int32_t)acc;
   p->total_tiles = (int32_t)acc;
-  cudaError_t e = cudaMemcpy(p->d_images, bi.data(), sizeof(BatchImage) * p->n, cudaMemcpyHostToDevice);
+  p->k_uniform = p->n ? p->images[0].k : 0;
+  for (int32_t i = 1; i < p->n; ++i)
+    if (p->images[i].k != p->k_uniform) p->k_uniform = -1;
+  return FDS_OK;
+}
+
+// device tables of the plan in its current order (synchronous copy)
+int upload_schedule(fds_plan* p) {
+  std::vector<BatchImage> bi(p->n + 1);
+  std::vector<int32_t> ts(p->n + 1);
+  int rc = build_tables(p, bi.data(), ts.data());
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (p->staged) e = cudaEventSynchronize(p->staged);   // an update may still be copying
+  if (e == cudaSuccess && p->n)
+    e = cudaMemcpy(p->d_images, bi.data(), sizeof(BatchImage) * p->n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tile_start, ts.data(), sizeof(int32_t) * (p->n + 1), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "plan upload");
   drop_graphs(p);
@@ -577,10 +592,8 @@ int fds_plan_create(const fds_image* images, int32_t n, fds_plan** plan_out) {
   if (!p) return set_err(FDS_E_NOMEM, "host allocation failed");
   p->dev = dev;
   p->n = n;
+  p->capacity = n;
   p->images.assign(images, images + n);
-  p->k_uniform = images[0].k;
-  for (int32_t i = 1; i < n; ++i)
-    if (images[i].k != p->k_uniform) p->k_uniform = -1;
   const size_t img_bytes = (sizeof(BatchImage) * n + 255) & ~(size_t)255;
   const size_t ts_bytes = (sizeof(int32_t) * (n + 1) + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(&p->mem, img_bytes + ts_bytes + 256);
@@ -605,7 +618,64 @@ int fds_plan_destroy(fds_plan* plan) {
   cudaDeviceSynchronize();
   drop_graphs(plan);
   cudaFree(plan->mem);
+  if (plan->host) cudaFreeHost(plan->host);
+  if (plan->staged) cudaEventDestroy(plan->staged);
   delete plan;
+  return FDS_OK;
+}
+
+int fds_plan_reserve(int32_t capacity, fds_plan** plan_out) {
+  if (!plan_out) return set_err(FDS_E_INVALID, "null plan pointer");
+  *plan_out = nullptr;
+  if (capacity < 1 || capacity > (1 << 20)) return set_err(FDS_E_INVALID, "capacity must be 1 .. 2^20");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  fds_plan* p = new (std::nothrow) fds_plan();
+  if (!p) return set_err(FDS_E_NOMEM, "host allocation failed");
+  p->dev = dev;
+  p->capacity = capacity;
+  const size_t img_bytes = (sizeof(BatchImage) * capacity + 255) & ~(size_t)255;
+  const size_t ts_bytes = (sizeof(int32_t) * (capacity + 1) + 255) & ~(size_t)255;
+  cudaError_t e = cudaMalloc(&p->mem, img_bytes + ts_bytes + 256);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->host, img_bytes + ts_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->staged, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fds_plan_destroy(p);
+    return set_err(FDS_E_NOMEM, std::string("plan allocation failed: ") + cudaGetErrorString(e));
+  }
+  p->d_images = static_cast<BatchImage*>(p->mem);
+  p->d_tile_start = reinterpret_cast<int32_t*>(static_cast<char*>(p->mem) + img_bytes);
+  p->d_dispenser = reinterpret_cast<unsigned int*>(static_cast<char*>(p->mem) + img_bytes + ts_bytes);
+  *plan_out = p;
+  return FDS_OK;
+}
+
+int fds_plan_update(fds_plan* plan, const fds_image* images, int32_t n, void* stream) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  if (!plan->host) return set_err(FDS_E_INVALID, "only plans made by fds_plan_reserve can be updated");
+  if (n < 0 || n > plan->capacity) return set_err(FDS_E_INVALID, "more images than the plan's capacity");
+  int rc = plan_device(plan);
+  if (rc) return rc;
+  if (n > 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((rc = check_descs(images, n))) return rc;
+  }
+  cudaError_t e = cudaEventSynchronize(plan->staged);   // previous copy has left the staging
+  if (e != cudaSuccess) return cuda_fail(e, "staging wait");
+  plan->images.assign(images, images + n);
+  plan->n = n;
+  const size_t img_bytes = (sizeof(BatchImage) * plan->capacity + 255) & ~(size_t)255;
+  BatchImage* bi = static_cast<BatchImage*>(plan->host);
+  int32_t* ts = reinterpret_cast<int32_t*>(static_cast<char*>(plan->host) + img_bytes);
+  if ((rc = build_tables(plan, bi, ts))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n) e = cudaMemcpyAsync(plan->d_images, bi, sizeof(BatchImage) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_tile_start, ts, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(plan->staged, s);
+  if (e != cudaSuccess) return cuda_fail(e, "plan update");
+  drop_graphs(plan);
   return FDS_OK;
 }
 

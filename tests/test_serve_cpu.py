@@ -1,0 +1,119 @@
+"""The serving scheduler's host logic on the CPU: lanes are fakes that compute each batch with
+the CPU oracle, so batching by kind, admission by memory, lane reuse and futures are tested
+without a GPU."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from oracle import aes as oaes, fds as ofds
+from paper_1512_02951_gb300 import synth
+
+KEYS = [synth.make_key(700 + i) for i in range(4)]
+
+
+class FakeLane:
+    """Finishes a batch a little after launch; records what the scheduler did."""
+    log = []
+    lock = threading.Lock()
+
+    def __init__(self, server_ref):
+        self.server_ref = server_ref
+        self.batch = None
+        self.t_done = 0.0
+
+    def busy(self):
+        return self.batch is not None
+
+    def done(self):
+        return self.batch is not None and time.perf_counter() >= self.t_done
+
+    def launch(self, batch):
+        srv = self.server_ref[0]
+        with FakeLane.lock:
+            FakeLane.log.append((len(batch), {r.kind for r in batch}, srv.in_use))
+        self.batch = batch
+        self.t_done = time.perf_counter() + 0.003
+
+    def finish(self):
+        res = []
+        for r in self.batch:
+            key = KEYS[r.key_slot]
+            if r.kind == "protect":
+                res.append((r, ofds.protect(np.asarray(r.pixels), key, r.iv, r.k)))
+            else:
+                res.append((r, ofds.restore(r.public, r.private, key, r.iv, r.k, r.width, r.height)))
+        self.batch = None
+        return res
+
+
+def _requests(n, seed):
+    from paper_1512_02951_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        w, h = int(rng.integers(1, 9)) * 8, int(rng.integers(1, 9)) * 8
+        k = int(rng.choice([0, 5]))
+        slot = int(rng.integers(0, len(KEYS)))
+        iv = synth.make_iv(seed + i)
+        img = synth.make_image(w, h, seed + i)
+        if rng.random() < 0.5:
+            reqs.append(Request("protect", w, h, k, slot, iv, pixels=img))
+        else:
+            pub, priv = ofds.protect(img, KEYS[slot], iv, k)
+            reqs.append(Request("restore", w, h, k, slot, iv, public=pub, private=priv))
+    return reqs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    from paper_1512_02951_gb300 import build
+    build.build()
+
+
+def test_scheduler_batches_by_kind_and_respects_memory():
+    from paper_1512_02951_gb300.serve import Server
+    FakeLane.log.clear()
+    reqs = _requests(60, 5)
+    budget = max(r.device_bytes() for r in reqs) * 3
+    ref = [None]
+    srv = Server(lanes=2, max_batch=8, mem_budget=budget, lane_factory=lambda i: FakeLane(ref))
+    ref[0] = srv
+    for r in reqs:
+        srv.submit(r)
+    for r in reqs:
+        got = r.future.result(timeout=60)
+        key = KEYS[r.key_slot]
+        if r.kind == "protect":
+            pub, priv = ofds.protect(np.asarray(r.pixels), key, r.iv, r.k)
+            assert np.array_equal(got[0], pub) and got[1] == priv
+        else:
+            want = ofds.restore(r.public, r.private, key, r.iv, r.k, r.width, r.height)
+            assert np.array_equal(got, want)
+    srv.close()
+    assert srv.in_use == 0
+    assert sum(n for n, _, _ in FakeLane.log) == len(reqs)
+    assert all(len(kinds) == 1 for _, kinds, _ in FakeLane.log)       # one kind per batch
+    assert max(n for n, _, _ in FakeLane.log) <= 8
+    assert max(u for _, _, u in FakeLane.log) <= budget                # admission by memory
+    assert srv.stats["max_batch"] > 1                                   # batching happened
+
+
+def test_oversized_request_is_rejected():
+    from paper_1512_02951_gb300.serve import Server
+    reqs = _requests(1, 9)
+    ref = [None]
+    srv = Server(lanes=1, mem_budget=reqs[0].device_bytes() - 1, lane_factory=lambda i: FakeLane(ref))
+    ref[0] = srv
+    with pytest.raises(ValueError):
+        srv.submit(reqs[0])
+    srv.close()
+
+
+def test_restore_request_ciphertext_is_what_ctr_gives():
+    # the fake lane's restore inputs are consistent with an independent CTR decryption
+    reqs = [r for r in _requests(20, 3) if r.kind == "restore"]
+    r = reqs[0]
+    plain = oaes.ctr_xcrypt(KEYS[r.key_slot], r.iv, r.private)
+    assert len(plain) == ofds.sizes(r.width, r.height, r.k)[1]
