@@ -202,6 +202,38 @@ int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_out, uint8_
 int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
                       float* coefs_out, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Tensor-core precision form of fds_protect_image (Sect. 6.4.2 transform as a matrix
+ * product).  The 8x8 DCT-II of 128 channel-blocks at a time is one tcgen05 MMA: pixels
+ * (exact in the operand type) times the orthonormal basis split into integer limbs,
+ * FP32 accumulate:
+ *   FDS_TC_BF16: basis = (L0 + L1 2^-8 + L2 2^-16) 2^-9, bf16 operands, three limbs
+ *   FDS_TC_TF32: basis = (L0 + L1 2^-11) 2^-12, tf32 operands, two limbs
+ * The accumulators hold exact integers; the coefficient error before rounding is at most
+ * 2.3e-4 (BF16) resp. 7.2e-4 (TF32), and every value within 2^-11 (2^-10) of a rounding
+ * boundary is re-decided exactly, so the outputs are bit-identical to fds_protect_image.
+ * Arguments, layouts and errors as fds_protect_image, and 3 (W/8)(H/8) < 2^31.  A
+ * tensor-core wait that gives up (bounded) adds 1 to counter 2 of fds_counters and leaves
+ * the outputs incomplete. */
+#define FDS_TC_BF16 0
+#define FDS_TC_TF32 1
+int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height,
+                         int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                         int16_t* public_out, uint8_t* private_out, void* stream);
+
+/* Diagnostics (host only, no device needed): the tensor-core form's B operand as the kernel
+ * holds it in shared memory -- row n = 64 l + 8u + v is limb l of the basis function
+ * (u, v), K index 8y + x, 128-byte rows, 16-byte chunk c of row n stored at chunk c ^ (n & 7);
+ * the TF32 form stores K 0..31 and K 32..63 as two consecutive 128-row blocks.  out: host,
+ * at least 24576 (BF16) or 32768 (TF32) bytes, or NULL.  *error_bound (host, or NULL): the
+ * proven bound on |computed - exact| of a pre-rounding coefficient of 8-bit pixels. */
+int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound);
+
+/* Diagnostics: the pre-rounding coefficients of the tensor-core form, laid out as in
+ * fds_debug_dct_f32.  coefs_out: device. */
+int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height,
+                     float* coefs_out, void* stream);
+
 /* Diagnostics: counters of the exact-rounding fallbacks taken since the last reset:
  * out[0] = values within the float32 error guard of a rounding boundary, re-decided from
  * their exact integer coordinates in Z[cos(pi/16)]; out[1] = of those, values whose 128-bit

@@ -16,6 +16,8 @@ FDS_E_TIMEOUT = -5
 FDS_E_BUSY = -6
 FDS_MAX_KEYS = 256
 FDS_NOALLOC_MAX_IMAGES = 4096
+FDS_TC_BF16 = 0
+FDS_TC_TF32 = 1
 
 _c_u8p = ctypes.POINTER(ctypes.c_uint8)
 
@@ -73,6 +75,14 @@ SIGNATURES = {
                                                  ctypes.c_void_p]),
     "fds_debug_dct_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "fds_protect_image_tc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                                            ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "fds_tc_basis": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64,
+                                    ctypes.POINTER(ctypes.c_double)]),
+    "fds_debug_dct_tc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "fds_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "fds_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "fds_last_error": (ctypes.c_char_p, []),

@@ -78,6 +78,37 @@ def protect_image(pixels: torch.Tensor, key: bytes, iv: bytes, k: int,
     return public_out, private_out
 
 
+TC_FORMS = {"bf16": _lib.FDS_TC_BF16, "tf32": _lib.FDS_TC_TF32}
+
+
+def _tc_form(form: str) -> int:
+    if form not in TC_FORMS:
+        raise ValueError(f"form must be one of {sorted(TC_FORMS)}")
+    return TC_FORMS[form]
+
+
+def protect_image_tc(pixels: torch.Tensor, key: bytes, iv: bytes, k: int, form: str = "bf16",
+                     public_out: torch.Tensor | None = None,
+                     private_out: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """fds_protect_image_tc: the tensor-core precision form ("bf16" three-limb or "tf32"
+    two-limb basis split); same outputs as protect_image, bit for bit."""
+    f = _tc_form(form)
+    w, h = _image_dims(pixels)
+    pub_b, priv_b = sizes(w, h, k)
+    dev = pixels.device
+    if public_out is None:
+        public_out = torch.empty((h // 8, w // 8, 3, 63 - k), dtype=torch.int16, device=dev)
+    if private_out is None:
+        private_out = torch.empty(priv_b, dtype=torch.uint8, device=dev)
+    assert public_out.numel() * 2 == pub_b and private_out.numel() == priv_b
+    rc = _lib.load().fds_protect_image_tc(
+        f, pixels.data_ptr(), w, h, k, _check_key(key, "key"), _check_key(iv, "iv"),
+        public_out.data_ptr() if public_out.numel() else None, private_out.data_ptr(),
+        _stream_ptr(dev))
+    _lib.check(rc, "fds_protect_image_tc")
+    return public_out, private_out
+
+
 def restore_image(public: torch.Tensor, private: torch.Tensor, width: int, height: int, k: int,
                   key: bytes, iv: bytes, pixels_out: torch.Tensor | None = None) -> torch.Tensor:
     """fds_restore_image: returns the H x W x 3 uint8 image."""
@@ -156,6 +187,29 @@ def debug_dct_f32(pixels: torch.Tensor) -> torch.Tensor:
     rc = _lib.load().fds_debug_dct_f32(pixels.data_ptr(), w, h, out.data_ptr(),
                                        _stream_ptr(pixels.device))
     _lib.check(rc, "fds_debug_dct_f32")
+    return out
+
+
+def tc_basis(form: str = "bf16") -> tuple[bytes, float]:
+    """fds_tc_basis (host only): the tensor-core B operand bytes and the proven bound on the
+    pre-rounding coefficient error."""
+    f = _tc_form(form)
+    n = 24576 if f == _lib.FDS_TC_BF16 else 32768
+    buf = (ctypes.c_uint8 * n)()
+    bound = ctypes.c_double()
+    _lib.check(_lib.load().fds_tc_basis(f, buf, n, ctypes.byref(bound)), "fds_tc_basis")
+    return bytes(buf), bound.value
+
+
+def debug_dct_tc(pixels: torch.Tensor, form: str = "bf16") -> torch.Tensor:
+    """fds_debug_dct_tc: the tensor-core form's float32 coefficients [H/8, W/8, 3, 8, 8]
+    before rounding."""
+    f = _tc_form(form)
+    w, h = _image_dims(pixels)
+    out = torch.empty((h // 8, w // 8, 3, 8, 8), dtype=torch.float32, device=pixels.device)
+    rc = _lib.load().fds_debug_dct_tc(f, pixels.data_ptr(), w, h, out.data_ptr(),
+                                      _stream_ptr(pixels.device))
+    _lib.check(rc, "fds_debug_dct_tc")
     return out
 
 

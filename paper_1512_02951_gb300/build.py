@@ -1,6 +1,6 @@
 """Build the CUDA library libfds.so in-tree (sm_103a only).
 
-The three translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 paper_1512_02951_gb300/_build/libfds.so.  The CUDA runtime is linked statically, so the
 library needs only the NVIDIA driver at run time.
 """
@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfds.so")
-UNITS = ("fds_api", "fds_protect", "fds_restore")
+UNITS = ("fds_api", "fds_protect", "fds_restore", "fds_protect_tc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                  "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

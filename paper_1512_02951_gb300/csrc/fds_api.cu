@@ -30,6 +30,9 @@ __device__ __align__(16) uint32_t g_rk[FDS_MAX_KEYS * 44];
 __device__ __align__(16) uint32_t g_cfwd[64 * 128];
 __device__ __align__(16) uint32_t g_cinv[64 * 128];
 __device__ unsigned long long g_counters[3];
+//  g_tcb0/1   tensor-core B operands (basis limbs, BF16 / TF32) in shared-memory byte order
+__device__ __align__(16) uint4 g_tcb0[kTcBBytesBf16 / 16];
+__device__ __align__(16) uint4 g_tcb1[kTcBBytesTf32 / 16];
 
 __global__ void init_tables_kernel() {
   const int t = threadIdx.x;
@@ -55,6 +58,7 @@ struct DevTables {
   const uint32_t* cinv;
   const uint32_t* round_keys;
   unsigned long long* counters;
+  const uint4* tc_b[2];
   int sms;
 };
 DevTables g_tables[kMaxDevices];
@@ -98,6 +102,74 @@ void iv_words(const uint8_t iv[16], uint64_t* hi, uint64_t* lo) {
   for (int i = 8; i < 16; ++i) l = (l << 8) | iv[i];
   *hi = h;
   *lo = l;
+}
+
+// Tensor-core B operand of form 0 (BF16, limbs 2^9, 2^8, 2^8) or 1 (TF32, limbs 2^12, 2^11):
+// row n = 64 l + (8u + v) holds limb l of b_u(y) b_v(x) at K index 8y + x, laid out as the
+// kernel's 128-byte swizzled K-major shared-memory image.  Returns false (with a message)
+// unless every assumption of the kernel's exactness argument holds: limbs exact in the
+// operand type, integer accumulators below 2^24, rational coefficients in limb 0 alone, and
+// split remainder + combining roundings below the kernel's rounding guard.
+bool build_tc_b(int form, std::vector<uint8_t>& img, std::string& why, double* bound_out = nullptr) {
+  const int nl = form == 0 ? 3 : 2;
+  const int sh[3] = {form == 0 ? 9 : 12, form == 0 ? 8 : 11, 8};
+  const int tot = form == 0 ? 25 : 23;                // sum of the shifts
+  const double guard = form == 0 ? 1.0 / 2048 : 1.0 / 1024;
+  const double lmax = form == 0 ? 256.0 : 2048.0;      // integers exact in bf16 / tf32
+  img.assign(form == 0 ? kTcBBytesBf16 : kTcBBytesTf32, 0);
+  double b[8][8];
+  for (int u = 0; u < 8; ++u)
+    for (int y = 0; y < 8; ++y) b[u][y] = (u == 0 ? std::sqrt(0.5) : 1.0) * 0.5 * std::cos((2 * y + 1) * u * std::acos(-1.0) / 16);
+  double rem_max = 0, fmax = 0, accmax = 0;
+  for (int pos = 0; pos < 64; ++pos) {
+    const int u = pos >> 3, v = pos & 7;
+    const bool rational = (u == 0 || u == 4) && (v == 0 || v == 4);
+    double rem = 0, fpos = 0, fneg = 0, lsum[3] = {0, 0, 0};
+    for (int kk = 0; kk < 64; ++kk) {
+      const double B = b[u][kk >> 3] * b[v][kk & 7];
+      (B > 0 ? fpos : fneg) += std::fabs(B);
+      double r = std::ldexp(B, sh[0]);
+      double L[3] = {0, 0, 0};
+      for (int l = 0; l < nl; ++l) {
+        if (l) r = std::ldexp(r, sh[l]);
+        L[l] = std::nearbyint(r);
+        r -= L[l];
+        lsum[l] += std::fabs(L[l]);
+        if (std::fabs(L[l]) > lmax) return (why = "limb not exact in the operand type"), false;
+      }
+      if (rational && (std::fabs(L[0]) != std::ldexp(1.0, sh[0] - 3) || L[1] != 0 || L[2] != 0))
+        return (why = "rational coefficient not carried by limb 0 alone"), false;
+      rem += std::ldexp(std::fabs(r), -tot);
+      for (int l = 0; l < nl; ++l) {
+        const int n = 64 * l + pos;
+        if (form == 0) {
+          const float f = (float)L[l];
+          uint32_t bits;
+          std::memcpy(&bits, &f, 4);
+          const uint16_t h = (uint16_t)(bits >> 16);
+          const int off = n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2;
+          std::memcpy(&img[off], &h, 2);
+        } else {
+          const float f = (float)L[l];
+          const int atom = kk >> 5, k2 = kk & 31;
+          const int off = atom * 128 * 128 + n * 128 + (((k2 >> 2) ^ (n & 7)) << 4) + (k2 & 3) * 4;
+          std::memcpy(&img[off], &f, 4);
+        }
+      }
+    }
+    rem_max = std::max(rem_max, 255.0 * rem);
+    if (!rational) fmax = std::max(fmax, 255.0 * std::max(fpos, fneg));
+    for (int l = 0; l < nl; ++l) accmax = std::max(accmax, 255.0 * lsum[l]);
+  }
+  if (accmax >= 16777216.0) return (why = "accumulator may exceed 2^24"), false;
+  // combining roundings: half an ulp of s = F 2^sh0 (and of the inner sum, BF16), scaled back
+  auto half_ulp = [](double x) { return std::ldexp(1.0, (int)std::floor(std::log2(x)) - 24); };
+  double comb = std::ldexp(half_ulp(fmax * std::ldexp(1.0, sh[0]) * 1.001), -sh[0]);
+  if (form == 0) comb += std::ldexp(half_ulp(accmax * 1.004), -17);
+  const double slack = 64.0 * 255.0 * std::ldexp(1.0, -50);   // cos() and B in double
+  if (bound_out) *bound_out = rem_max + comb + slack;
+  if (rem_max + comb + slack >= guard) return (why = "limb split exceeds the rounding guard"), false;
+  return true;
 }
 
 // Initialise the current device (once) and return its index in *dev_out.
@@ -176,6 +248,21 @@ int ensure_init(int* dev_out = nullptr) {
   tb.counters = static_cast<unsigned long long*>(p);
   if ((e = cudaGetSymbolAddress(&p, g_rk)) != cudaSuccess) return cuda_fail(e, "symbol address");
   tb.round_keys = static_cast<const uint32_t*>(p);
+  {
+    static std::vector<uint8_t> tcb[2];
+    static bool tcb_ok[2];
+    static std::string tcb_why[2];
+    for (int f = 0; f < 2; ++f) {
+      if (tcb[f].empty()) tcb_ok[f] = build_tc_b(f, tcb[f], tcb_why[f]);
+      if (!tcb_ok[f]) return set_err(FDS_E_INVALID, "tensor-core table: " + tcb_why[f]);
+    }
+    if ((e = cudaMemcpyToSymbol(g_tcb0, tcb[0].data(), tcb[0].size())) != cudaSuccess) return cuda_fail(e, "table upload");
+    if ((e = cudaMemcpyToSymbol(g_tcb1, tcb[1].data(), tcb[1].size())) != cudaSuccess) return cuda_fail(e, "table upload");
+    if ((e = cudaGetSymbolAddress(&p, g_tcb0)) != cudaSuccess) return cuda_fail(e, "symbol address");
+    tb.tc_b[0] = static_cast<const uint4*>(p);
+    if ((e = cudaGetSymbolAddress(&p, g_tcb1)) != cudaSuccess) return cuda_fail(e, "symbol address");
+    tb.tc_b[1] = static_cast<const uint4*>(p);
+  }
   for (int i = 0; i < FDS_MAX_KEYS; ++i)   // keys registered before this device was ready
     if (g_slots[i].used &&
         (e = cudaMemcpyToSymbol(g_rk, g_slots[i].rk, sizeof(g_slots[i].rk), 44 * 4 * i)) != cudaSuccess)
@@ -382,6 +469,68 @@ int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height, floa
   a.dbg_coefs = coefs_out;
   fill_geometry(a, width, height, 0);
   return run_protect(a, dev, (cudaStream_t)stream, true);
+}
+
+int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height, int32_t k,
+                         const uint8_t key[16], const uint8_t iv[16], int16_t* public_out,
+                         uint8_t* private_out, void* stream) {
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  if (bad_dims(width, height) || 3ll * (width / 8) * (height / 8) >= (1ll << 31))
+    return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8, 3 W H / 64 < 2^31");
+  if (k < 0 || k > 63) return set_err(FDS_E_INVALID, "k must be in 0..63");
+  if (!pixels || !key || !iv || !private_out || (k < 63 && !public_out))
+    return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(pixels, 8) || misaligned(public_out, 16) || misaligned(private_out, 16))
+    return set_err(FDS_E_INVALID, "pixels must be 8-byte aligned, fragments 16-byte aligned");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  TileArgs a{};
+  a.pixels_in = pixels;
+  a.pub_out = public_out;
+  a.priv_out = private_out;
+  fill_geometry(a, width, height, k);
+  expand_key(key, a.rk);
+  iv_words(iv, &a.iv_hi, &a.iv_lo);
+  set_tables(a, dev);
+  a.tc_b = g_tables[dev].tc_b[form];
+  const cudaError_t e = launch_protect_tc(a, (cudaStream_t)stream, form, false, g_tables[dev].sms);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core protect launch");
+}
+
+int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  std::vector<uint8_t> img;
+  std::string why;
+  double bound = 0;
+  const bool ok = build_tc_b(form, img, why, &bound);
+  if (error_bound) *error_bound = bound;
+  if (!ok) return set_err(FDS_E_INVALID, "tensor-core table: " + why);
+  if (out) {
+    if (bytes < img.size()) return set_err(FDS_E_INVALID, "output buffer too small");
+    std::memcpy(out, img.data(), img.size());
+  }
+  return FDS_OK;
+}
+
+int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height, float* coefs_out,
+                     void* stream) {
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  if (bad_dims(width, height) || 3ll * (width / 8) * (height / 8) >= (1ll << 31))
+    return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8, 3 W H / 64 < 2^31");
+  if (!pixels || !coefs_out) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(pixels, 8) || misaligned(coefs_out, 4)) return set_err(FDS_E_INVALID, "misaligned buffer");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  TileArgs a{};
+  a.pixels_in = pixels;
+  a.dbg_coefs = coefs_out;
+  fill_geometry(a, width, height, 0);
+  set_tables(a, dev);
+  a.tc_b = g_tables[dev].tc_b[form];
+  const cudaError_t e = launch_protect_tc(a, (cudaStream_t)stream, form, true, g_tables[dev].sms);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core debug launch");
 }
 
 int fds_counters(uint64_t* out, int reset) {

@@ -27,6 +27,10 @@ constexpr int kCoefBytes = kTileCb * 128;      // public + private int16 staging
 constexpr int kQueueCap = 256;                 // near-tie entries per tile
 constexpr int kCtasPerSm = 2;
 
+// tensor-core form: bytes of the B operand (basis limbs) in shared memory
+constexpr int kTcBBytesBf16 = 192 * 128;      // 3 limbs x 64 rows x 64 bf16
+constexpr int kTcBBytesTf32 = 2 * 128 * 128;  // 2 limbs x 64 rows x 64 tf32, as two K atoms
+
 // Forward guard.  On level-shifted pixels |p - 128| <= 128 the butterflies are within
 // 1.11e-3 of the exact coefficient (first-order bound: every rounded operation and every
 // rounded constant, each weighted by the output's sensitivity to it).  2^-9 = 1.95e-3.
@@ -65,6 +69,8 @@ struct TileArgs {
   const uint32_t* round_keys;     // device, FDS_MAX_KEYS x 44 words
   unsigned int* dispenser;        // device tile counter (dynamic dispatch), or null (static)
   int32_t n_images, total_tiles;
+  // tensor-core form: the B operand (basis limbs) in its shared-memory byte order (device)
+  const uint4* tc_b;
 };
 
 // What a CTA knows about the tile it is working on (shared memory, filled one tile ahead).
@@ -85,6 +91,9 @@ struct TileSlot {
 // resident CTAs per SM to launch (1 or 2)
 cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 2);
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 2);
+// tensor-core protect of one image (form 0: BF16 three limbs, 1: TF32 two limbs); tiles of
+// 128 channel-blocks, two CTAs per SM
+cudaError_t launch_protect_tc(const TileArgs& a, cudaStream_t s, int form, bool debug, int sms);
 
 inline int total_tiles(const TileArgs& a) {
   return a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
@@ -181,9 +190,10 @@ __device__ __forceinline__ int next_tile(const TileArgs& a, int i) {
 
 // 24-byte block row of the pixel tile shifted right by `c` bytes: channel c's pixel x is
 // then byte 3x of the result (w[0..5] little-endian)
+template <int ROWB = kRowBytes>
 __device__ __forceinline__ void load_row_shifted(const uint8_t* tile, int y, int b, int c,
                                                  uint32_t (&w)[6]) {
-  const uint2* rp = reinterpret_cast<const uint2*>(tile + y * kRowBytes + b * 24);
+  const uint2* rp = reinterpret_cast<const uint2*>(tile + y * ROWB + b * 24);
   const uint2 w01 = rp[0], w23 = rp[1], w45 = rp[2];
   const uint32_t r[7] = {w01.x, w01.y, w23.x, w23.y, w45.x, w45.y, 0u};
 #pragma unroll
@@ -213,13 +223,15 @@ __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_
 // Exact integer coordinates of 8 F[u][v] (pos = 8u+v) of channel c of tile block b:
 // n[j] = sum over the 64 pixels of pixel * K_j, with the signed-byte weights K_j of
 // table[pos][j][16 words] (word w covers pixels x = 4(w&1) .. +3 of row w>>1).
+// ROWB: bytes per pixel row of the tile
+template <int ROWB = kRowBytes>
 __device__ __forceinline__ void coords_fwd(const uint8_t* tile, int b, int c, int pos,
                                            const uint32_t* table, int (&n)[9]) {
   uint32_t P[16];
 #pragma unroll
   for (int y = 0; y < 8; ++y) {
     uint32_t w[6];
-    load_row_shifted(tile, y, b, c, w);
+    load_row_shifted<ROWB>(tile, y, b, c, w);
     // bytes 0, 3, 6, 9 and 12, 15, 18, 21 of w
     P[2 * y] = __byte_perm(__byte_perm(w[0], w[1], 0x0630u), w[2], 0x5210u);
     P[2 * y + 1] = __byte_perm(__byte_perm(w[3], w[4], 0x0630u), w[5], 0x5210u);
