@@ -93,6 +93,30 @@ __device__ __forceinline__ void dct8_row_bytes(const float (&X)[8], float (&x)[8
   dct8_sd<true, false>(s, d, x);
 }
 
+// Error weight of one 8-point pass over exact inputs: |d_0| + .. + |d_3| + |f_0| + |f_1| with
+// f_0 = s_0 - s_3, f_1 = s_1 - s_2 (small integers, so the sum is exact).  The rounding error
+// of every irrational output of the pass is at most 2.46 u times this weight (u = 2^-24).
+__device__ __forceinline__ float pass_weight(const float (&s)[4], const float (&d)[4]) {
+  return ((fabsf(d[0]) + fabsf(d[1])) + (fabsf(d[2]) + fabsf(d[3]))) + (fabsf(s[0] - s[3]) + fabsf(s[1] - s[2]));
+}
+
+// dct8_row_bytes that also returns the row's error weight
+__device__ __forceinline__ float dct8_row_bytes_w(const float (&X)[8], float (&x)[8]) {
+  constexpr float c2 = 16777472.0f;  // 2^24 + 256
+  const float s[4] = {(X[0] - c2) + X[7], (X[1] - c2) + X[6], (X[2] - c2) + X[5], (X[3] - c2) + X[4]};
+  const float d[4] = {X[0] - X[7], X[1] - X[6], X[2] - X[5], X[3] - X[4]};
+  dct8_sd<true, false>(s, d, x);
+  return pass_weight(s, d);
+}
+
+// dct8<true, true> of an exact-integer column that also returns its error weight
+__device__ __forceinline__ float dct8_rat_w(float (&x)[8]) {
+  const float s[4] = {x[0] + x[7], x[1] + x[6], x[2] + x[5], x[3] + x[4]};
+  const float d[4] = {x[0] - x[7], x[1] - x[6], x[2] - x[5], x[3] - x[4]};
+  dct8_sd<true, true>(s, d, x);
+  return pass_weight(s, d);
+}
+
 // Inverse: X (orthonormal coefficients) -> x_n = sum_k b_k(n) X_k.
 __device__ __forceinline__ void idct8(float (&x)[8]) {
   constexpr float lam = (float)kLambda;

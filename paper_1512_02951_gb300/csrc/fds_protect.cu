@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
     if (b < nb) {
       float f[8][8];
+      float V = 0.0f, W = 0.0f;   // error weights of the row passes and of columns 0, 4
 #pragma unroll
       for (int y = 0; y < 8; ++y) {
         uint32_t w[6];
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
           const int byte = 3 * x;
           X[x] = __int_as_float(__byte_perm(w[byte >> 2], 0x4B000000u, 0x7440u | (byte & 3)));
         }
-        dct8_row_bytes(X, f[y]);
+        V += dct8_row_bytes_w(X, f[y]);
       }
       // columns; columns 0 and 4 hold unscaled (exact integer) row outputs
 #pragma unroll
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
 #pragma unroll
         for (int y = 0; y < 8; ++y) col[y] = f[y][v];
         if (v == 0 || v == 4)
-          dct8<true, true>(col);
+          W += dct8_rat_w(col);
         else
           dct8<false, false>(col);
 #pragma unroll
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
         int16_t* pub_cb = pubst + cb * npub;
         int16_t* priv_cb = privst + cb * (k + 1);
         uint32_t mlo = 0, mhi = 0;
+        const float thr = 0.5f - fminf(fmaf(V, kGuardV, fmaf(W, kGuardW, kGuardU)), kGuardFwd);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
             } else {
               const float yv = f[u][v] + kMagic;
               q = __float_as_uint(yv);                 // low 16 bits: the int16 result
-              if (fabsf(f[u][v] - (yv - kMagic)) > 0.5f - kGuardFwd) {
+              if (fabsf(f[u][v] - (yv - kMagic)) > thr) {
                 if (8 * u + v < 32)
                   mlo |= 1u << (8 * u + v);
                 else

@@ -35,6 +35,19 @@ constexpr int kTcBBytesTf32 = 2 * 128 * 128;  // 2 limbs x 64 rows x 64 tf32, as
 // 1.11e-3 of the exact coefficient (first-order bound: every rounded operation and every
 // rounded constant, each weighted by the output's sensitivity to it).  2^-9 = 1.95e-3.
 constexpr float kGuardFwd = 1.0f / 512.0f;
+// Tighter per channel-block forward guard, from the data.  With u = 2^-24, V = sum over the 8
+// rows of the row pass's error weight and W = the weights of the column passes of columns 0
+// and 4 (exact integer inputs; see pass_weight):
+//  - a row pass output is exact (columns 0, 4) or within 2.46 u V_y of exact, and its
+//    magnitude is at most 0.4904 V_y;
+//  - a column pass over columns 1-3, 5-7 adds at most 0.4904 sum_y 2.46 u V_y for its
+//    inputs' errors and 2.95 u sum_y |input| <= 1.45 u V of its own, so |F - exact| <= 2.65 u V;
+//  - columns 0 and 4 start from exact integers: |F - exact| <= 0.87 u W (scaled constants).
+// G = u (2.7 V + 0.9 W + 1) bounds every coefficient's error (the extra u covers the rounding
+// of 0.5 - G and of G itself); min(G, kGuardFwd) is used.
+constexpr float kGuardV = 2.7f / 16777216.0f;
+constexpr float kGuardW = 0.9f / 16777216.0f;
+constexpr float kGuardU = 1.0f / 16777216.0f;
 // Inverse guard per channel-block: error <= 2.89 u sum|F| (u = 2^-24); 2^-22 sum|F| is used.
 constexpr float kGuardInvScale = 1.0f / 4194304.0f;
 

@@ -132,6 +132,31 @@ def test_float32_coefficients_within_1e3(api):
         assert err < 1.0 / 512                          # the guard the kernel relies on
 
 
+def _pass_weight(x):
+    """sum_i<4 |x_i - x_7-i| + |(x0 + x7) - (x3 + x4)| + |(x1 + x6) - (x2 + x5)| over the last
+    axis (exact integers)."""
+    d = np.abs(x[..., :4] - x[..., 7:3:-1]).sum(axis=-1)
+    s = x[..., :4] + x[..., 7:3:-1]
+    return d + np.abs(s[..., 0] - s[..., 3]) + np.abs(s[..., 1] - s[..., 2])
+
+
+def test_float32_error_within_data_dependent_guard(api):
+    # the per-block guard u (2.7 V + 0.9 W + 1) that the protect kernel uses: V from the rows,
+    # W from the exact-integer columns 0 and 4 of the row pass
+    u = 2.0 ** -24
+    for img in (synth.make_image(256, 128, 5), _adversarial_image(), synth.make_image(64, 64, 9)):
+        got = api.debug_dct_f32(torch.from_numpy(img).to(DEV)).cpu().numpy().astype(np.float64)
+        blocks = odct.image_to_blocks(img).astype(np.int64)               # [by, bx, 3, 8, 8]
+        V = _pass_weight(blocks).sum(axis=-1)
+        x = blocks - 128
+        col0 = x.sum(axis=-1)                                              # row sums
+        col4 = x[..., [0, 3, 4, 7]].sum(axis=-1) - x[..., [1, 2, 5, 6]].sum(axis=-1)
+        W = _pass_weight(col0) + _pass_weight(col4)
+        bound = u * (2.7 * V + 0.9 * W + 1)
+        err = np.abs(got - odct.dct2(blocks)).max(axis=(-1, -2))
+        assert np.all(err <= bound), float((err / bound).max())
+
+
 def test_restore_of_arbitrary_int16_fragments(api):
     # restore must be exact for any int16 input, not only for what protect produces
     rng = np.random.default_rng(9)
