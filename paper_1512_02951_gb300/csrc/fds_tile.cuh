@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "fds_device.cuh"
@@ -57,6 +58,8 @@ struct BatchImage {
   int32_t width, height, k, key_slot;
   uint64_t iv_hi, iv_lo;
 };
+static_assert(sizeof(BatchImage) == 56 && offsetof(BatchImage, width) == 24 && offsetof(BatchImage, iv_hi) == 40,
+              "BatchImage layout");
 
 // Kernel arguments.  Single image: `images` is null and the image fields describe it.
 // Batch: the pointers are the batch buffers, images[i] gives each image's offsets, and
