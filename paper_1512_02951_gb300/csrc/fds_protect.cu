@@ -11,14 +11,16 @@
 //      coefficients within the float32 error guard of a half-integer are queued
 //   B. 2. queued coefficients are re-decided exactly (integer coordinates in Z[cos(pi/16)])
 //   C. 3. AES-128-CTR over the private staging area, one thread per 16-byte keystream block
-// Staging is double-buffered so a tile's stores overlap the next tile's transform.
+// One staging area (so that three CTAs fit on an SM): the previous tile's bulk stores must
+// have read it before the transform writes it again.
 #include "fds_tile.cuh"
 
 namespace fds {
 
+constexpr int kPCtasPerSm = 3;
 constexpr int kSmemPix = 0;                                  // 2 pixel tiles
-constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 2 staging areas
-constexpr int kSmemT = kSmemStage + 2 * kCoefBytes;          // AES tables, 4 KB
+constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 1 staging area
+constexpr int kSmemT = kSmemStage + kCoefBytes;              // AES tables, 4 KB
 constexpr int kSmemQueue = kSmemT + 4096;                    // near-tie queue
 constexpr int kSmemSlot = kSmemQueue + 4 * kQueueCap;        // 3 tile slots (ring)
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
@@ -56,7 +58,7 @@ __device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
 // from the kernel parameters, which AES then takes as constant-bank operands)
 template <int K, bool DEBUG, bool BATCH>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
+__global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
@@ -88,22 +90,23 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
     const TileSlot* sl = slot(s_cur);
     if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot(s_nxt));
     cp_async_wait_all();
-    if (t == 0) {
-      if (!DEBUG) bulk_wait_read_all();   // staging[buf] is no longer read by older stores
-      misc[0] = 0;
-    }
+    if (t == 0) misc[0] = 0;
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
-    if (!DEBUG && t == 0 && have_prev)
-      store_fragments(slot(s_prev), smem + kSmemStage + (buf ^ 1) * kCoefBytes);
+    if (!DEBUG && t == 0 && have_prev) {
+      store_fragments(slot(s_prev), smem + kSmemStage);
+      bulk_wait_read_all();                  // the staging area may be written again
+    }
+    __syncthreads();                                                       // A'
+
     if (nxt < ntiles) load_pixels(slot(s_nxt), smem + kSmemPix + (buf ^ 1) * kPixBytes);
 
     const int k = K >= 0 ? K : sl->k;
     const int npub = 63 - k;
     const int nb = sl->nb;
     const uint8_t* tile_px = smem + kSmemPix + buf * kPixBytes;
-    int16_t* pubst = reinterpret_cast<int16_t*>(smem + kSmemStage + buf * kCoefBytes);
-    int16_t* privst = reinterpret_cast<int16_t*>(smem + kSmemStage + buf * kCoefBytes + kTileCb * 2 * npub);
+    int16_t* pubst = reinterpret_cast<int16_t*>(smem + kSmemStage);
+    int16_t* privst = reinterpret_cast<int16_t*>(smem + kSmemStage + kTileCb * 2 * npub);
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
     if (b < nb) {
       float f[8][8];
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) protect_kernel(const __g
   if (DEBUG) return;
   __syncthreads();
   if (t == 0) {
-    if (have_prev) store_fragments(slot((it + 2) % 3), smem + kSmemStage + ((it - 1) & 1) * kCoefBytes);
+    if (have_prev) store_fragments(slot((it + 2) % 3), smem + kSmemStage);
     bulk_wait_all();
     if (a.counters) {
       if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
@@ -257,7 +260,7 @@ static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_
     attr = true;
   }
   const int ntiles = total_tiles(a);
-  const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
+  const int cap = (per_sm == 1 ? 1 : kPCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
   if (grid > 0) protect_kernel<K, DEBUG, BATCH><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
