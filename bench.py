@@ -141,13 +141,23 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _kernel_source_sha():
+# the sources each kernel is compiled from (its translation unit and the shared headers)
+KERNEL_SOURCES = {
+    "protect_kernel": ["fds_protect.cu"],
+    "restore_kernel": ["fds_restore.cu"],
+    "protect_tc_kernel": ["fds_protect_tc.cu"],
+}
+SHARED_HEADERS = ["fds_tile.cuh", "fds_device.cuh", "fds_cos_limbs.h"]
+
+
+def kernel_source_sha(kernel):
+    """Short hash of the sources of one kernel; a committed ncu summary applies only while it
+    matches."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1512_02951_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(fh.read())
+    for name in KERNEL_SOURCES[kernel] + SHARED_HEADERS:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -161,7 +171,7 @@ def _profiled_traffic(kernel):
         return None
     sha = re.search(r"source_sha:\s*([0-9a-f]+)", text)
     tr = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
-    if not sha or not tr or sha.group(1) != _kernel_source_sha():
+    if not sha or not tr or sha.group(1) != kernel_source_sha(kernel):
         return None
     return int(tr.group(1))
 
