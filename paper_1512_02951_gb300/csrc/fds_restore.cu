@@ -9,16 +9,19 @@
 //   1. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
 //      into the interleaved pixel tile; values within the float32 error guard of a
 //      half-integer are queued
-//   B. 2. queued pixels are re-decided exactly (integer coordinates in Z[cos(pi/16)])
-//   C. 3. the pixel tile goes to global memory with 8-byte stores, and the next tile's
-//      private range is decrypted in place (AES-128-CTR)
+//   B. 2. queued pixels are re-decided exactly (integer coordinates in Z[cos(pi/16)]) by the
+//      last threads while the first ones decrypt the next tile's private range in place
+//      (AES-128-CTR)
+//   C. 3. the pixel tile goes to global memory: one bulk (TMA engine) store per pixel row when
+//      the tile's rows are contiguous and 16-byte aligned, else 8-byte stores.  The pixel tile
+//      is double-buffered so the bulk stores overlap the next tile.
 #include "fds_tile.cuh"
 
 namespace fds {
 
 constexpr int kSmemCoef = 0;                                 // 2 fragment staging areas
-constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 1 pixel tile
-constexpr int kSmemQueue = kSmemPix + kPixBytes;
+constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 2 pixel tiles
+constexpr int kSmemQueue = kSmemPix + 2 * kPixBytes;
 constexpr int kSmemSlot = kSmemQueue + 4 * kQueueCap;        // 3 tile slots (ring)
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
@@ -73,7 +76,6 @@ template <int K, bool BATCH>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) uint32_t Ts[1024];                // AES T-tables
-  uint8_t* pix = smem + kSmemPix;
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
   // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
@@ -103,7 +105,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     if (cur >= ntiles) break;
     const TileSlot* sl = slot(it % 3);
     if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot((it + 1) % 3));
-    if (t == 0) misc[0] = 0;
+    uint8_t* pix = smem + kSmemPix + buf * kPixBytes;
+    if (t == 0) {
+      misc[0] = 0;
+      // the stores of two tiles ago have read pix (each tile commits one bulk group)
+      asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+    }
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
     if (nxt < ntiles) load_fragments(slot((it + 1) % 3), stage(buf ^ 1));
@@ -175,8 +182,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     cp_async_wait_all();                                  // this thread's copies of `next`
     __syncthreads();                                                       // B
     {
+      // queued pixels (from the last thread down) re-decided exactly while the first threads
+      // decrypt the next tile's private range
       const int nq = min(misc[0], kQueueCap);
-      for (int i = t; i < nq; i += kThreads) {
+      for (int i = kThreads - 1 - t; i < nq; i += kThreads) {
         const uint32_t e = queue[i];
         const int ecb = (int)(e >> 8), pos = (int)(e & 255);
         const int eb = ecb / 3, ec = ecb - 3 * eb;
@@ -189,22 +198,40 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       }
       if (t == 0) misc[1] += misc[0];
     }
+    if (nxt < ntiles) decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
+    fence_proxy_async();                                  // pixel writes before the bulk stores
     __syncthreads();                                                       // C
     {
+      // the pixel tile to global memory: one bulk (TMA engine) store per pixel row when the
+      // tile's blocks are contiguous and 16-byte aligned in every row, else 8-byte stores
       const uint64_t w3 = (uint64_t)sl->width * 3ull;
-      for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
-        const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
-        const int bb = rem / 3, q = rem - 3 * bb;
-        if (bb < nb)
-          *reinterpret_cast<uint2*>(sl->px_out + sl->blk[bb] + y * w3 + 8 * q) =
-              *reinterpret_cast<const uint2*>(pix + y * kRowBytes + bb * 24 + 8 * q);
+      const int bxc = sl->width >> 3;
+      const int bx0 = (sl->local * kTileBlocks) % bxc;
+      uint8_t* row0 = sl->px_out + sl->blk[0];
+      const bool bulk = bx0 + nb <= bxc && ((nb * 24) & 15) == 0 && (w3 & 15) == 0 &&
+                        (reinterpret_cast<uintptr_t>(row0) & 15) == 0;
+      if (bulk) {
+        if (t == 0) {
+#pragma unroll 1
+          for (int y = 0; y < 8; ++y) bulk_store(row0 + y * w3, pix + y * kRowBytes, (uint32_t)(nb * 24));
+          bulk_commit();
+        }
+      } else {
+        if (t == 0) bulk_commit();               // an empty group keeps one group per tile
+        for (int i = t; i < 8 * kTileBlocks * 3; i += kThreads) {
+          const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
+          const int bb = rem / 3, q = rem - 3 * bb;
+          if (bb < nb)
+            *reinterpret_cast<uint2*>(sl->px_out + sl->blk[bb] + y * w3 + 8 * q) =
+                *reinterpret_cast<const uint2*>(pix + y * kRowBytes + bb * 24 + 8 * q);
+        }
       }
     }
-    if (nxt < ntiles) decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
   }
   if (esc) atomicAdd(&misc[2], esc);
   if (fail) atomicAdd(&misc[3], 1);
   __syncthreads();
+  if (t == 0) bulk_wait_all();
   if (t == 0 && a.counters) {
     if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
     if (misc[2]) atomicAdd(&a.counters[1], (unsigned long long)misc[2]);
