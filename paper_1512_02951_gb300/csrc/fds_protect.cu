@@ -10,7 +10,8 @@
 //      int16 and written to the public or private staging area at its zigzag position;
 //      coefficients within the float32 error guard of a half-integer are queued
 //   B. 2. queued coefficients are re-decided exactly (integer coordinates in Z[cos(pi/16)])
-//   C. 3. AES-128-CTR over the private staging area, one thread per 16-byte keystream block
+//   C. 3. the public fragment leaves (bulk store) while AES-128-CTR encrypts the private
+//      staging area, one thread per 16-byte keystream block
 // One staging area (so that three CTAs fit on an SM): the previous tile's bulk stores must
 // have read it before the transform writes it again.
 #include "fds_tile.cuh"
@@ -27,18 +28,24 @@ constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
 constexpr int kSmemBytes = kSmemMisc + 32;
 
-// the fragments staged for slot sl (buffer st) to global memory; one thread
-__device__ __forceinline__ void store_fragments(const TileSlot* sl, const uint8_t* st) {
+// the public / private fragment staged for slot sl (staging area st) to global memory, one
+// bulk group each; one thread
+__device__ __forceinline__ void store_public(const TileSlot* sl, const uint8_t* st) {
   const int k = sl->k, npub = 63 - k, nb = sl->nb;
-  const int pub_bytes = nb * 6 * npub, priv_bytes = nb * 6 * (k + 1);
+  const int pub_bytes = nb * 6 * npub;
   uint8_t* pdst = sl->pub_out + (uint64_t)sl->local * kTileBlocks * 6ull * npub;
-  uint8_t* vdst = sl->priv_out + (uint64_t)sl->local * kTileBlocks * 6ull * (k + 1);
-  const uint8_t* vsrc = st + kTileCb * 2 * npub;
   if (pub_bytes >> 4) bulk_store(pdst, st, (uint32_t)(pub_bytes & ~15));
-  if (priv_bytes >> 4) bulk_store(vdst, vsrc, (uint32_t)(priv_bytes & ~15));
   bulk_commit();
   for (int j = pub_bytes & ~15; j < pub_bytes; j += 2)
     *reinterpret_cast<uint16_t*>(pdst + j) = *reinterpret_cast<const uint16_t*>(st + j);
+}
+__device__ __forceinline__ void store_private(const TileSlot* sl, const uint8_t* st) {
+  const int k = sl->k, npub = 63 - k, nb = sl->nb;
+  const int priv_bytes = nb * 6 * (k + 1);
+  uint8_t* vdst = sl->priv_out + (uint64_t)sl->local * kTileBlocks * 6ull * (k + 1);
+  const uint8_t* vsrc = st + kTileCb * 2 * npub;
+  if (priv_bytes >> 4) bulk_store(vdst, vsrc, (uint32_t)(priv_bytes & ~15));
+  bulk_commit();
   for (int j = priv_bytes & ~15; j < priv_bytes; j += 2)
     *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
 }
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
     if (!DEBUG && t == 0 && have_prev) {
-      store_fragments(slot(s_prev), smem + kSmemStage);
+      store_private(slot(s_prev), smem + kSmemStage);   // the public part left before its AES
       bulk_wait_read_all();                  // the staging area may be written again
     }
     __syncthreads();                                                       // A'
@@ -230,7 +237,9 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
       if (fail) atomicAdd(&misc[3], 1);
       if (t == 0) misc[1] += misc[0];
     }
+    fence_proxy_async();                   // every thread's staging writes, before the bulk store
     __syncthreads();                                                       // C
+    if (t == 0) store_public(sl, smem + kSmemStage);   // final: it leaves during the AES
     ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
              ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
              BATCH ? sl->rk : a.rk, Ts);
@@ -240,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
   if (DEBUG) return;
   __syncthreads();
   if (t == 0) {
-    if (have_prev) store_fragments(slot((it + 2) % 3), smem + kSmemStage);
+    if (have_prev) store_private(slot((it + 2) % 3), smem + kSmemStage);
     bulk_wait_all();
     if (a.counters) {
       if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);

@@ -36,7 +36,6 @@ constexpr int kTcMaxBlocks = 44;              // blocks a run of 128 channel-blo
 constexpr int kTcRowB = kTcMaxBlocks * 24;    // one pixel row of the tile
 constexpr int kTcPixBytes = 8 * kTcRowB;
 constexpr int kTcCoefBytes = kTcCb * 128;     // public + private int16 staging
-constexpr uint32_t kMbarSpinLimit = 1u << 22; // bounded waits (seconds at most): give up, flag it
 
 template <int FORM>
 struct TcForm;
@@ -90,20 +89,6 @@ __device__ __forceinline__ uint32_t sw128_chunk(int row, int chunk) {
   return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-// bounded wait for phase `parity`; false if it did not complete in time
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok = 0;
-  for (uint32_t i = 0; i < kMbarSpinLimit && !ok; ++i)
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 "selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
-                 : "memory");
-  return ok != 0;
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
