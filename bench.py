@@ -568,6 +568,69 @@ def precision_arm(args):
 
 
 # ------------------------------------------------------------------------------------------
+# selective vs full encryption (the paper's comparison, Tables 7, 9, 11) on the same GPU
+def compare_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_1512_02951_gb300 import api, build, synth
+
+    build.build()
+    api.init(0)
+    dev = torch.device("cuda", 0)
+    img_np = synth.make_image(WIDTH, HEIGHT, IMG_SEED)
+    img = torch.from_numpy(img_np).to(dev)
+    key, iv = synth.make_key(KEY_SEED), synth.make_iv(IV_SEED)
+    px_bytes = WIDTH * HEIGHT * 3
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    full_out = torch.empty_like(img)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)                                  # L2 flushed between timed launches
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    res = {}
+    full_ms = timed(lambda: api.encrypt_full(img, key, iv, out=full_out))
+    res["full_aes128_ctr"] = {"ms": round(full_ms, 5), "MBps": round(px_bytes / (full_ms * 1e-3) / 1e6, 1)}
+    for k in (0, 5):
+        pub_b, priv_b = api.sizes(WIDTH, HEIGHT, k)
+        pub = torch.empty((HEIGHT // 8, WIDTH // 8, 3, 63 - k), dtype=torch.int16, device=dev)
+        priv = torch.empty(priv_b, dtype=torch.uint8, device=dev)
+        out = torch.empty_like(img)
+        p_ms = timed(lambda: api.protect_image(img, key, iv, k, pub, priv))
+        r_ms = timed(lambda: api.restore_image(pub, priv, WIDTH, HEIGHT, k, key, iv, out))
+        res[f"selective_k{k}"] = {"protect_ms": round(p_ms, 5), "restore_ms": round(r_ms, 5),
+                                  "protect_MBps": round(px_bytes / (p_ms * 1e-3) / 1e6, 1),
+                                  "encrypted_bytes": priv_b,
+                                  "protect_time_vs_full_encryption": round(p_ms / full_ms, 3)}
+    peak, _ = _peaks()
+    full_gbs = 2 * px_bytes / (full_ms * 1e-3) / 1e9
+    line = {"metric": "selective protection vs full AES-128-CTR of the pixels, MB/s of pixels",
+            "value": res["selective_k5"]["protect_MBps"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["selective_k5"]["protect_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{WIDTH}x{HEIGHT} RGB uint8: protect (k=0, 5) vs AES-128-CTR of all "
+                                   "pixel bytes", "l2": "256 MB buffer written between timed launches"},
+            "results": res,
+            "full_encryption_roofline": {"bound": "hbm", "achieved": round(full_gbs, 1), "peak": peak,
+                                         "unit": "GB/s", "frac": round(full_gbs / peak, 4)},
+            "gpu_launches": args.steps * 5}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # serving form: Poisson arrivals, mixed protect / restore, continuous batching
 SERVE_N, SERVE_RATE, SERVE_SEED = 1500, 500.0, 4242
 
@@ -633,7 +696,7 @@ def serve_arm(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["image4096", "precision", "batch2000", "serve"],
+    ap.add_argument("--workload", choices=["image4096", "precision", "compare", "batch2000", "serve"],
                     default="image4096")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -653,6 +716,8 @@ def main():
         reference_arm(args)
     elif args.workload == "precision":
         precision_arm(args)
+    elif args.workload == "compare":
+        compare_arm(args)
     elif args.workload == "batch2000":
         batch_arm(args)
     elif args.workload == "serve":

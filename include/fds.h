@@ -196,6 +196,15 @@ int fds_plan_restore_graph(fds_plan* plan, const int16_t* public_in, const uint8
 int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
                               const fds_image* images, int32_t n, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Full encryption, the paper's comparator for selective encryption (Sect. 6.5, Tables 7, 9,
+ * 11: the whole bitmap encrypted): AES-128-CTR over `bytes` bytes, the same keystream
+ * convention as the private fragment (block j = AES_K(IV + j), 128-bit big-endian counter).
+ * in, out: device, 16-byte aligned; in == out encrypts in place, other overlaps are
+ * rejected.  key, iv: host, 16 bytes each.  Decryption is the same call. */
+int fds_encrypt_full(const uint8_t* in, uint8_t* out, uint64_t bytes, const uint8_t key[16],
+                     const uint8_t iv[16], void* stream);
+
 /* Diagnostics: the float32 coefficients the protect kernel computes before rounding, as
  * float [H/8][W/8][3][8][8] ([u][v] inside a block).  coefs_out: device.  Used to compare
  * the pre-rounding values with a float64 reference (Sect. 6.4.3 precision concern). */

@@ -190,6 +190,23 @@ def debug_dct_f32(pixels: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def encrypt_full(data: torch.Tensor, key: bytes, iv: bytes,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_encrypt_full: AES-128-CTR over the whole byte buffer (the full-encryption
+    comparator); `out` may be `data` itself."""
+    flat = data.reshape(-1).view(torch.uint8)
+    if out is None:
+        out = torch.empty_like(flat)
+    dst = out.reshape(-1).view(torch.uint8)
+    assert dst.numel() == flat.numel()
+    rc = _lib.load().fds_encrypt_full(flat.data_ptr() if flat.numel() else None,
+                                      dst.data_ptr() if dst.numel() else None, flat.numel(),
+                                      _check_key(key, "key"), _check_key(iv, "iv"),
+                                      _stream_ptr(data.device))
+    _lib.check(rc, "fds_encrypt_full")
+    return out
+
+
 def tc_basis(form: str = "bf16") -> tuple[bytes, float]:
     """fds_tc_basis (host only): the tensor-core B operand bytes and the proven bound on the
     pre-rounding coefficient error."""

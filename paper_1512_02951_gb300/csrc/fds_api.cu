@@ -498,6 +498,25 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core protect launch");
 }
 
+int fds_encrypt_full(const uint8_t* in, uint8_t* out, uint64_t bytes, const uint8_t key[16], const uint8_t iv[16],
+                     void* stream) {
+  if (!key || !iv || (bytes && (!in || !out))) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(in, 16) || misaligned(out, 16)) return set_err(FDS_E_INVALID, "buffers must be 16-byte aligned");
+  if (in != out && bytes && (const uint8_t*)out < in + bytes && in < (const uint8_t*)out + bytes)
+    return set_err(FDS_E_INVALID, "buffers overlap without being the same");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  if (!bytes) return FDS_OK;
+  uint32_t rk[44];
+  expand_key(key, rk);
+  uint64_t hi, lo;
+  iv_words(iv, &hi, &lo);
+  const cudaError_t e = launch_aes_full(in, out, bytes, hi, lo, rk, g_tables[dev].T, (cudaStream_t)stream,
+                                        g_tables[dev].sms);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "full encryption launch");
+}
+
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {
   if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
   std::vector<uint8_t> img;

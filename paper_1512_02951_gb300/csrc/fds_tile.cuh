@@ -107,6 +107,9 @@ struct TileSlot {
 // resident CTAs per SM to launch (1 or 2)
 cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 2);
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 2);
+// AES-128-CTR over a whole buffer (the full-encryption comparator)
+cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
+                            const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms);
 // tensor-core protect of one image (form 0: BF16 three limbs, 1: TF32 two limbs); tiles of
 // 128 channel-blocks, two CTAs per SM
 cudaError_t launch_protect_tc(const TileArgs& a, cudaStream_t s, int form, bool debug, int sms);

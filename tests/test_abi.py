@@ -115,3 +115,13 @@ def test_plan_arguments_are_checked_on_the_host(lib):
     assert lib.fds_plan_create(d, 1, ctypes.byref(h)) in (-1, -2)           # misaligned offset
     assert lib.fds_plan_set_schedule(None, 1, 0, 0) == -1
     assert lib.fds_plan_destroy(None) == 0
+
+
+def test_full_encryption_arguments_are_checked_on_the_host(lib):
+    key = bytes(16)
+    assert lib.fds_encrypt_full(None, 16, 32, key, key, None) == -1          # null input
+    assert lib.fds_encrypt_full(24, 32, 32, key, key, None) == -1            # not 16-aligned
+    assert b"aligned" in lib.fds_last_error()
+    assert lib.fds_encrypt_full(32, 48, 64, key, key, None) == -1            # partial overlap
+    assert b"overlap" in lib.fds_last_error()
+    assert lib.fds_encrypt_full(32, 32, 64, None, key, None) == -1           # null key
