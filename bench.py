@@ -146,6 +146,7 @@ KERNEL_SOURCES = {
     "protect_kernel": ["fds_protect.cu"],
     "restore_kernel": ["fds_restore.cu"],
     "protect_tc_kernel": ["fds_protect_tc.cu"],
+    "aes_ctr_full_kernel": ["fds_aes_full.cu"],
 }
 SHARED_HEADERS = ["fds_tile.cuh", "fds_device.cuh", "fds_cos_limbs.h"]
 

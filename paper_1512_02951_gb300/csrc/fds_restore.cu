@@ -5,7 +5,7 @@
 // Persistent CTAs over a tile schedule (one image, or every tile of a batch of images in one
 // launch); per tile (see fds_tile.cuh for the decomposition):
 //   A. the tile's fragments are in shared memory, already decrypted; the next tile's start
-//      loading (cp.async)
+//      loading (one bulk copy per fragment range, or cp.async pieces)
 //   1. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
 //      into the interleaved pixel tile; values within the float32 error guard of a
 //      half-integer are queued
@@ -24,7 +24,8 @@ constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 2 pixel tiles
 constexpr int kSmemQueue = kSmemPix + 2 * kPixBytes;
 constexpr int kSmemSlot = kSmemQueue + 4 * kQueueCap;        // 3 tile slots (ring)
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
-constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
+constexpr int kSmemBar = kSmemSlot + 3 * kSlotBytes;         // 2 mbarriers (staging areas)
+constexpr int kSmemMisc = kSmemBar + 16;
 constexpr int kSmemBytes = kSmemMisc + 32;
 
 // gather the 64 int16 coefficients of tile channel-block cb in zigzag order, two per word
@@ -41,13 +42,29 @@ __device__ __forceinline__ void gather_coefs(const int16_t* pubst, const int16_t
 }
 
 // cp.async the public and private ranges of slot sl's tile into staging area st
-__device__ __forceinline__ void load_fragments(const TileSlot* sl, uint8_t* st) {
+// True if both fragment ranges of the tile are whole 16-byte units (then each arrives as one
+// bulk copy completing on an mbarrier; else as 16-byte cp.async pieces)
+__device__ __forceinline__ bool frag_bulk(const TileSlot* sl) {
+  const int k = sl->k, nb = sl->nb;
+  return ((nb * 6 * (63 - k)) & 15) == 0 && ((nb * 6 * (k + 1)) & 15) == 0;
+}
+// Load the public and private ranges of slot sl's tile into staging area st (all threads call
+// it; thread 0 issues the bulk copies)
+__device__ __forceinline__ void load_fragments(const TileSlot* sl, uint8_t* st, uint64_t* bar) {
   const int t = threadIdx.x;
   const int k = sl->k, npub = 63 - k, nb = sl->nb;
   const int pub_bytes = nb * 6 * npub, priv_bytes = nb * 6 * (k + 1);
   const uint8_t* psrc = sl->pub_in + (uint64_t)sl->local * kTileBlocks * 6ull * npub;
   const uint8_t* vsrc = sl->priv_in + (uint64_t)sl->local * kTileBlocks * 6ull * (k + 1);
   uint8_t* vdst = st + kTileCb * 2 * npub;
+  if (frag_bulk(sl)) {
+    if (t == 0) {
+      mbar_expect_tx(bar, (uint32_t)(pub_bytes + priv_bytes));
+      if (pub_bytes) bulk_load(st, psrc, (uint32_t)pub_bytes, bar);
+      bulk_load(vdst, vsrc, (uint32_t)priv_bytes, bar);
+    }
+    return;
+  }
   const int p16 = pub_bytes >> 4, v16 = priv_bytes >> 4;
   for (int i = t; i < p16 + v16; i += kThreads) {
     if (i < p16)
@@ -60,6 +77,16 @@ __device__ __forceinline__ void load_fragments(const TileSlot* sl, uint8_t* st) 
   for (int j = (v16 << 4) + 2 * t; j < priv_bytes; j += 2 * kThreads)
     *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
   cp_async_commit();
+}
+// Wait until this thread may read what load_fragments loaded (a barrier must follow);
+// phase: the next phase of bar; lost counts bulk loads that did not complete in time
+__device__ __forceinline__ void wait_fragments(const TileSlot* sl, uint64_t* bar, uint32_t& phase, int& lost) {
+  if (frag_bulk(sl)) {
+    if (!mbar_wait(bar, phase)) ++lost;
+    phase ^= 1u;
+  } else {
+    cp_async_wait_all();
+  }
 }
 
 // CTR decryption of the private range of slot sl's tile, in staging area st
@@ -93,8 +120,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
   }
   if (t < kTileBlocks) fill_slot(a, blockIdx.x, slot(0));
   __syncthreads();
-  load_fragments(slot(0), stage(0));
-  cp_async_wait_all();
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  uint32_t phase[2] = {0u, 0u};
+  int lost = 0;
+  if (t == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  load_fragments(slot(0), stage(0), bars);
+  wait_fragments(slot(0), bars, phase[0], lost);
   __syncthreads();
   decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
   int esc = 0;
@@ -113,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     }
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
-    if (nxt < ntiles) load_fragments(slot((it + 1) % 3), stage(buf ^ 1));
+    if (nxt < ntiles) load_fragments(slot((it + 1) % 3), stage(buf ^ 1), bars + (buf ^ 1));
     const int k = K >= 0 ? K : sl->k;
     const int npub = 63 - k;
     const int nb = sl->nb;
@@ -179,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         }
       }
     }
-    cp_async_wait_all();                                  // this thread's copies of `next`
+    if (nxt < ntiles) wait_fragments(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
     __syncthreads();                                                       // B
     {
       // queued pixels (from the last thread down) re-decided exactly while the first threads
@@ -229,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     }
   }
   if (esc) atomicAdd(&misc[2], esc);
-  if (fail) atomicAdd(&misc[3], 1);
+  if (fail || lost) atomicAdd(&misc[3], 1);
   __syncthreads();
   if (t == 0) bulk_wait_all();
   if (t == 0 && a.counters) {
