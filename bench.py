@@ -62,7 +62,7 @@ def _oracle_child(args):
     rows = args.rows
     bx = WIDTH // 8
     done_bytes, t_used, times = 0, 0.0, []
-    r0 = 0
+    r0 = args.start_row
     while r0 < HEIGHT // 8 and (t_used < args.budget or not times) and len(times) < args.max_steps:
         r1 = min(HEIGHT // 8, r0 + rows)
         strip = img[8 * r0: 8 * r1]
@@ -85,23 +85,61 @@ def _oracle_child(args):
                       "rows_per_step": rows, "times": times}))
 
 
-def _run_oracle(rows, budget, max_steps):
+def _oracle_cmd(rows, budget, max_steps, start_row=0):
+    return [sys.executable, os.path.abspath(__file__), "--oracle-child", "--rows", str(rows),
+            "--budget", str(budget), "--max-steps", str(max_steps), "--start-row", str(start_row)]
+
+
+def _oracle_env():
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--rows", str(rows),
-           "--budget", str(budget), "--max-steps", str(max_steps)]
-    out = subprocess.run(cmd, capture_output=True, text=True, env=env, check=True).stdout
+    return env
+
+
+def _run_oracle(rows, budget, max_steps):
+    out = subprocess.run(_oracle_cmd(rows, budget, max_steps), capture_output=True, text=True,
+                         env=_oracle_env(), check=True).stdout
     return json.loads(out.strip().splitlines()[-1])
+
+
+def _run_oracle_all_cores(rows, budget):
+    """One single-threaded oracle process per host core, each on its own strips, all at once;
+    throughput = all processes' bytes / the longest process time."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    nrows = HEIGHT // 8
+    procs = [subprocess.Popen(_oracle_cmd(rows, budget, 10 ** 6, (i * nrows // cores) // rows * rows),
+                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                              env=_oracle_env()) for i in range(cores)]
+    res = []
+    for p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle child failed")
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    total = sum(r["bytes"] for r in res)
+    secs = max(r["seconds"] for r in res)
+    return total, secs, cores
 
 
 def cpu_baseline():
     r = _run_oracle(rows=32, budget=20.0, max_steps=10 ** 6)
     mbps = r["bytes"] / r["seconds"] / 1e6
-    return {"value": round(mbps, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{r['steps']} strips of {r['rows_per_step']} block rows "
-                      f"({r['bytes'] / 1e6:.1f} MB of pixels) of the workload image, "
-                      "float64 numpy oracle, one thread"}
+    out = {"value": round(mbps, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{r['steps']} strips of {r['rows_per_step']} block rows "
+                     f"({r['bytes'] / 1e6:.1f} MB of pixels) of the workload image, "
+                     "float64 numpy oracle, one thread"}
+    try:
+        total, secs, cores = _run_oracle_all_cores(rows=8, budget=8.0)
+        out["all_cores"] = {"value": round(total / secs / 1e6, 3), "unit": UNIT, "cores": cores,
+                            "sample": f"{cores} single-threaded oracle processes on strips of 8 block "
+                                      f"rows ({total / 1e6:.1f} MB of pixels in all) for ~8 s each"}
+    except (OSError, RuntimeError, ValueError) as exc:
+        out["all_cores"] = {"unavailable": str(exc)}
+    return out
 
 
 def reference_arm(args):
@@ -708,6 +746,7 @@ def main():
     ap.add_argument("--rows", type=int, default=32, help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
     ap.add_argument("--max-steps", type=int, default=10 ** 6, help=argparse.SUPPRESS)
+    ap.add_argument("--start-row", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
