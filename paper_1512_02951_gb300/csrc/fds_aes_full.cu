@@ -88,13 +88,10 @@ __global__ void __launch_bounds__(kFullThreads) aes_ctr_full_kernel(const __grid
 // `sms` = number of SMs; grid = enough CTAs for the buffer, at most 4 per SM (32 KB table each)
 cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
                             const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms) {
-  static bool attr = false;
+  static bool attr[kMaxAttrDevices];
   constexpr int kSmem = kTrepWords * 4;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(aes_ctr_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = smem_attr_once(aes_ctr_full_kernel, kSmem, attr);
+  if (e != cudaSuccess) return e;
   FullArgs a{};
   a.in = in;
   a.out = out;

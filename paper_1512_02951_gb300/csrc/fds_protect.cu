@@ -261,13 +261,9 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
 
 template <int K, bool DEBUG, bool BATCH>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(protect_kernel<K, DEBUG, BATCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static bool attr[kMaxAttrDevices];
+  cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH>, kSmemBytes, attr);
+  if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
   const int cap = (per_sm == 1 ? 1 : kPCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;

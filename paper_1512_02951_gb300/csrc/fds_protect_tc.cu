@@ -424,13 +424,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) protect_tc_kernel(const __grid_
 
 template <int FORM, int K, bool DEBUG>
 static cudaError_t tc_launch_k(const TileArgs& a, cudaStream_t s, int sms) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(protect_tc_kernel<FORM, K, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcSmem<FORM>::kBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static bool attr[kMaxAttrDevices];
+  cudaError_t e = smem_attr_once(protect_tc_kernel<FORM, K, DEBUG>, TcSmem<FORM>::kBytes, attr);
+  if (e != cudaSuccess) return e;
   const long long ntiles = (3ll * a.nblocks + kTcCb - 1) / kTcCb;
   const long long grid = ntiles < 2ll * sms ? ntiles : 2ll * sms;
   if (grid > 0) protect_tc_kernel<FORM, K, DEBUG><<<(unsigned)grid, kTcThreads, TcSmem<FORM>::kBytes, s>>>(a);

@@ -277,13 +277,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
 
 template <int K, bool BATCH>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(restore_kernel<K, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static bool attr[kMaxAttrDevices];
+  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH>, kSmemBytes, attr);
+  if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
   const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;

@@ -114,6 +114,23 @@ cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uin
 // 128 channel-blocks, two CTAs per SM
 cudaError_t launch_protect_tc(const TileArgs& a, cudaStream_t s, int form, bool debug, int sms);
 
+// Raise a kernel's dynamic shared-memory limit once per device (the attribute is per
+// device; `done` is the launcher's own record)
+constexpr int kMaxAttrDevices = 64;
+template <typename Kernel>
+inline cudaError_t smem_attr_once(Kernel kernel, int bytes, bool (&done)[kMaxAttrDevices]) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxAttrDevices) return cudaErrorInvalidDevice;
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
 inline int total_tiles(const TileArgs& a) {
   return a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
 }
