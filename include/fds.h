@@ -230,6 +230,32 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
                          int32_t k, const uint8_t key[16], const uint8_t iv[16],
                          int16_t* public_out, uint8_t* private_out, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Bit-packed storage (Sect. 6.4.3, Table 5): both fragments as bit streams instead of int16
+ * words.  FDS_PACK_11 ("11-bit storage", lossless for 8-bit images): DC unsigned in 11 bits,
+ * every AC as a sign bit over a 10-bit magnitude.  FDS_PACK_8 ("8-bit storage", lossy): DC in
+ * 11 bits, AC as a sign bit over a 7-bit magnitude saturated at 127.  A field takes the next
+ * bits of its stream, least significant bit first (stream bit b = bit b % 8 of byte b / 8);
+ * channel-blocks in [by][bx][c] order, each with its fields in fragment order (zigzag k+1..63,
+ * resp. 0..k); the last byte is zero-padded.  The packed private stream is AES-128-CTR
+ * encrypted from the IV like the int16 one.
+ * fds_sizes_packed gives the packed fragment sizes and the device scratch the two calls need
+ * (the int16 fragments and, for restore, the decrypted packed stream).  Arguments otherwise
+ * as fds_protect_image / fds_restore_image; private and scratch 16-byte aligned, the packed
+ * public fragment at any alignment.  scratch: device, owned by the caller, overwritten. */
+#define FDS_PACK_11 11
+#define FDS_PACK_8 8
+int fds_sizes_packed(int32_t form, int32_t width, int32_t height, int32_t k,
+                     uint64_t* public_bytes, uint64_t* private_bytes, uint64_t* scratch_bytes);
+int fds_protect_image_packed(int32_t form, const uint8_t* pixels, int32_t width, int32_t height,
+                             int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                             uint8_t* public_out, uint8_t* private_out, void* scratch,
+                             void* stream);
+int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8_t* private_in,
+                             int32_t width, int32_t height, int32_t k, const uint8_t key[16],
+                             const uint8_t iv[16], uint8_t* pixels_out, void* scratch,
+                             void* stream);
+
 /* Diagnostics (host only, no device needed): the tensor-core form's B operand as the kernel
  * holds it in shared memory -- row n = 64 l + 8u + v is limb l of the basis function
  * (u, v), K index 8y + x, 128-byte rows, 16-byte chunk c of row n stored at chunk c ^ (n & 7);

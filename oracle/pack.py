@@ -86,8 +86,9 @@ def unpack_bits(data: bytes, widths: np.ndarray) -> np.ndarray:
 
 def decode(codes: np.ndarray, widths: np.ndarray, first_is_dc: bool, m: int) -> np.ndarray:
     """Signed values [n_cb, m] from field codes (inverse of fields_of, up to saturation)."""
-    c = codes.reshape(-1, m)
-    w = widths.reshape(-1, m)
+    n = codes.size // m if m else 0
+    c = codes.reshape(n, m)
+    w = widths.reshape(n, m)
     sign = (c >> (w - 1)) & 1
     mag = c & ((1 << (w - 1)) - 1)
     v = np.where(sign == 1, -mag, mag)
@@ -108,9 +109,10 @@ def sizes(width: int, height: int, k: int, form: int) -> tuple[int, int]:
 def protect_packed(img: np.ndarray, key: bytes, iv: bytes, k: int, form: int) -> tuple[bytes, bytes]:
     """The first level of protection with packed storage: (public bytes, private ciphertext)."""
     pub, priv = fds.protect(img, key, iv, k)
+    ncb = (img.shape[0] // 8) * (img.shape[1] // 8) * 3
     plain = np.frombuffer(aes.ctr_xcrypt(key, iv, priv), dtype="<i2").astype(np.int64)
-    part1 = plain.reshape(-1, k + 1)
-    part2 = np.asarray(pub, dtype=np.int64).reshape(-1, 63 - k)
+    part1 = plain.reshape(ncb, k + 1)
+    part2 = np.asarray(pub, dtype=np.int64).reshape(ncb, 63 - k)
     pub_codes, pub_w = fields_of(part2, False, form)
     priv_codes, priv_w = fields_of(part1, True, form)
     return pack_bits(pub_codes, pub_w), aes.ctr_xcrypt(key, iv, pack_bits(priv_codes, priv_w))
@@ -123,7 +125,7 @@ def restore_packed(public: bytes, private: bytes, key: bytes, iv: bytes, k: int,
     w = ac_bits(form)
     pub_w = np.full(ncb * (63 - k), w, dtype=np.int64)
     priv_w = np.tile(np.array([DC_BITS] + [w] * k, dtype=np.int64), ncb)
-    part2 = decode(unpack_bits(public, pub_w), pub_w, False, 63 - k)
+    part2 = decode(unpack_bits(public, pub_w), pub_w, False, 63 - k).reshape(ncb, 63 - k)
     plain = aes.ctr_xcrypt(key, iv, bytes(private))
     part1 = decode(unpack_bits(plain, priv_w), priv_w, True, k + 1)
     pub16 = part2.astype("<i2").reshape(height // 8, width // 8, 3, 63 - k)

@@ -18,6 +18,8 @@ FDS_MAX_KEYS = 256
 FDS_NOALLOC_MAX_IMAGES = 4096
 FDS_TC_BF16 = 0
 FDS_TC_TF32 = 1
+FDS_PACK_11 = 11
+FDS_PACK_8 = 8
 
 _c_u8p = ctypes.POINTER(ctypes.c_uint8)
 
@@ -79,6 +81,17 @@ SIGNATURES = {
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                                             ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
+    "fds_sizes_packed": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "fds_protect_image_packed": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                                                ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "fds_restore_image_packed": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_char_p, ctypes.c_char_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "fds_encrypt_full": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_char_p, ctypes.c_char_p, ctypes.c_void_p]),
     "fds_tc_basis": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64,

@@ -190,6 +190,49 @@ def debug_dct_f32(pixels: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def sizes_packed(width: int, height: int, k: int, form: int = 11) -> tuple[int, int, int]:
+    """fds_sizes_packed: (packed public bytes, packed private bytes, scratch bytes)."""
+    pub, priv, scr = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.check(_lib.load().fds_sizes_packed(form, width, height, k, ctypes.byref(pub), ctypes.byref(priv),
+                                            ctypes.byref(scr)), "fds_sizes_packed")
+    return pub.value, priv.value, scr.value
+
+
+def protect_image_packed(pixels: torch.Tensor, key: bytes, iv: bytes, k: int, form: int = 11,
+                         scratch: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """fds_protect_image_packed: (packed public bytes, packed private ciphertext) as uint8
+    device tensors (11-bit or 8-bit storage)."""
+    w, h = _image_dims(pixels)
+    pub_b, priv_b, scr_b = sizes_packed(w, h, k, form)
+    dev = pixels.device
+    pub = torch.empty(max(pub_b, 1), dtype=torch.uint8, device=dev)
+    priv = torch.empty(max(priv_b, 16), dtype=torch.uint8, device=dev)
+    if scratch is None:
+        scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
+    rc = _lib.load().fds_protect_image_packed(form, pixels.data_ptr(), w, h, k, _check_key(key, "key"),
+                                              _check_key(iv, "iv"), pub.data_ptr(), priv.data_ptr(),
+                                              scratch.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_protect_image_packed")
+    return pub[:pub_b], priv[:priv_b]
+
+
+def restore_image_packed(public: torch.Tensor, private: torch.Tensor, width: int, height: int, k: int,
+                         key: bytes, iv: bytes, form: int = 11,
+                         scratch: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_restore_image_packed: the H x W x 3 uint8 image."""
+    dev = private.device
+    _, _, scr_b = sizes_packed(width, height, k, form)
+    if scratch is None:
+        scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
+    out = torch.empty((height, width, 3), dtype=torch.uint8, device=dev)
+    rc = _lib.load().fds_restore_image_packed(form, public.data_ptr() if public.numel() else None,
+                                              private.data_ptr(), width, height, k, _check_key(key, "key"),
+                                              _check_key(iv, "iv"), out.data_ptr(), scratch.data_ptr(),
+                                              _stream_ptr(dev))
+    _lib.check(rc, "fds_restore_image_packed")
+    return out
+
+
 def encrypt_full(data: torch.Tensor, key: bytes, iv: bytes,
                  out: torch.Tensor | None = None) -> torch.Tensor:
     """fds_encrypt_full: AES-128-CTR over the whole byte buffer (the full-encryption

@@ -517,6 +517,102 @@ int fds_encrypt_full(const uint8_t* in, uint8_t* out, uint64_t bytes, const uint
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "full encryption launch");
 }
 
+// ---- bit-packed storage (Sect. 6.4.3, Table 5)
+static uint64_t align16u(uint64_t x) { return (x + 15) & ~15ull; }
+
+int fds_sizes_packed(int32_t form, int32_t width, int32_t height, int32_t k, uint64_t* public_bytes,
+                     uint64_t* private_bytes, uint64_t* scratch_bytes) {
+  if (form != FDS_PACK_11 && form != FDS_PACK_8) return set_err(FDS_E_INVALID, "form must be 11 or 8");
+  uint64_t pub16 = 0, priv16 = 0;
+  int rc = fds_sizes(width, height, k, &pub16, &priv16);
+  if (rc) return rc;
+  const uint64_t ncb = (uint64_t)(width / 8) * (uint64_t)(height / 8) * 3ull;
+  const uint64_t pub = (ncb * (uint64_t)(63 - k) * (uint64_t)form + 7) / 8;
+  const uint64_t priv = (ncb * (11ull + (uint64_t)k * (uint64_t)form) + 7) / 8;
+  if (public_bytes) *public_bytes = pub;
+  if (private_bytes) *private_bytes = priv;
+  if (scratch_bytes) *scratch_bytes = align16u(pub16) + align16u(priv16) + align16u(priv);
+  return FDS_OK;
+}
+
+static int packed_checks(int32_t form, int32_t width, int32_t height, int32_t k, const void* px, const void* pub,
+                         const void* priv, const void* scratch, uint64_t* pub16, uint64_t* priv16,
+                         uint64_t* priv_packed) {
+  if (form != FDS_PACK_11 && form != FDS_PACK_8) return set_err(FDS_E_INVALID, "form must be 11 or 8");
+  int rc = fds_sizes_packed(form, width, height, k, nullptr, priv_packed, nullptr);
+  if (rc) return rc;
+  if ((rc = fds_sizes(width, height, k, pub16, priv16))) return rc;
+  if (!px || !priv || !scratch || (k < 63 && !pub)) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(px, 8) || misaligned(priv, 16) || misaligned(scratch, 16))
+    return set_err(FDS_E_INVALID, "pixels must be 8-byte aligned, private and scratch 16-byte aligned");
+  return FDS_OK;
+}
+
+int fds_protect_image_packed(int32_t form, const uint8_t* pixels, int32_t width, int32_t height, int32_t k,
+                             const uint8_t key[16], const uint8_t iv[16], uint8_t* public_out, uint8_t* private_out,
+                             void* scratch, void* stream) {
+  uint64_t pub16 = 0, priv16 = 0, vpk = 0;
+  int rc = packed_checks(form, width, height, k, pixels, public_out, private_out, scratch, &pub16, &priv16, &vpk);
+  if (rc) return rc;
+  if (!key || !iv) return set_err(FDS_E_INVALID, "null pointer argument");
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int16_t* s_pub = static_cast<int16_t*>(scratch);
+  uint8_t* s_priv = static_cast<uint8_t*>(scratch) + align16u(pub16);
+  TileArgs a{};                                  // 1. the transform, private left in plaintext
+  a.pixels_in = pixels;
+  a.pub_out = s_pub;
+  a.priv_out = s_priv;
+  a.plain_private = 1;
+  fill_geometry(a, width, height, k);
+  expand_key(key, a.rk);
+  iv_words(iv, &a.iv_hi, &a.iv_lo);
+  if ((rc = run_protect(a, dev, s, false))) return rc;
+  const long long ncb = 3ll * a.nblocks;         // 2. pack both fragments
+  cudaError_t e = launch_pack(s_pub, reinterpret_cast<const int16_t*>(s_priv), public_out, private_out, ncb, k,
+                              form, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+  e = launch_aes_full(private_out, private_out, vpk, a.iv_hi, a.iv_lo, a.rk, g_tables[dev].T, s,
+                      g_tables[dev].sms);        // 3. encrypt the packed private stream
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "encryption launch");
+}
+
+int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8_t* private_in, int32_t width,
+                             int32_t height, int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                             uint8_t* pixels_out, void* scratch, void* stream) {
+  uint64_t pub16 = 0, priv16 = 0, vpk = 0;
+  int rc = packed_checks(form, width, height, k, pixels_out, public_in, private_in, scratch, &pub16, &priv16, &vpk);
+  if (rc) return rc;
+  if (!key || !iv) return set_err(FDS_E_INVALID, "null pointer argument");
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int16_t* s_pub = static_cast<int16_t*>(scratch);
+  uint8_t* s_priv = static_cast<uint8_t*>(scratch) + align16u(pub16);
+  uint8_t* s_plain = s_priv + align16u(priv16);
+  uint32_t rk[44];
+  expand_key(key, rk);
+  uint64_t hi, lo;
+  iv_words(iv, &hi, &lo);
+  cudaError_t e = launch_aes_full(private_in, s_plain, vpk, hi, lo, rk, g_tables[dev].T, s,
+                                  g_tables[dev].sms);   // 1. decrypt the packed private stream
+  if (e != cudaSuccess) return cuda_fail(e, "decryption launch");
+  const long long ncb = 3ll * (width / 8) * (long long)(height / 8);
+  e = launch_unpack(public_in, s_plain, s_pub, reinterpret_cast<int16_t*>(s_priv), ncb, k, form, s);
+  if (e != cudaSuccess) return cuda_fail(e, "unpack launch");   // 2. back to int16
+  TileArgs a{};                                  // 3. the inverse transform from plaintext
+  a.pub_in = s_pub;
+  a.priv_in = s_priv;
+  a.pixels_out = pixels_out;
+  a.plain_private = 1;
+  fill_geometry(a, width, height, k);
+  std::memcpy(a.rk, rk, sizeof(rk));
+  a.iv_hi = hi;
+  a.iv_lo = lo;
+  return run_restore(a, dev, s);
+}
+
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {
   if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
   std::vector<uint8_t> img;

@@ -240,9 +240,10 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     fence_proxy_async();                   // every thread's staging writes, before the bulk store
     __syncthreads();                                                       // C
     if (t == 0) store_public(sl, smem + kSmemStage);   // final: it leaves during the AES
-    ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
-             ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
-             BATCH ? sl->rk : a.rk, Ts);
+    if (!a.plain_private)
+      ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
+               ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
+               BATCH ? sl->rk : a.rk, Ts);
     fence_proxy_async();
     have_prev = true;
   }

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
   load_fragments(slot(0), stage(0), bars);
   wait_fragments(slot(0), bars, phase[0], lost);
   __syncthreads();
-  decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
+  if (!a.plain_private) decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
   int esc = 0;
   bool fail = false;
   for (int it = 0;; ++it) {
@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       }
       if (t == 0) misc[1] += misc[0];
     }
-    if (nxt < ntiles) decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
+    if (nxt < ntiles && !a.plain_private)
+      decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
     fence_proxy_async();                                  // pixel writes before the bulk stores
     __syncthreads();                                                       // C
     {

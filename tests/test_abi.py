@@ -125,3 +125,17 @@ def test_full_encryption_arguments_are_checked_on_the_host(lib):
     assert lib.fds_encrypt_full(32, 48, 64, key, key, None) == -1            # partial overlap
     assert b"overlap" in lib.fds_last_error()
     assert lib.fds_encrypt_full(32, 32, 64, None, key, None) == -1           # null key
+
+
+def test_packed_storage_sizes_and_checks(lib):
+    from oracle import pack
+    pub, priv, scr = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    for form in (11, 8):
+        for (w, h, k) in [(64, 48, 0), (520, 40, 5), (8, 8, 63)]:
+            assert lib.fds_sizes_packed(form, w, h, k, ctypes.byref(pub), ctypes.byref(priv), ctypes.byref(scr)) == 0
+            assert (pub.value, priv.value) == pack.sizes(w, h, k, form)
+            assert scr.value >= 2 * (w // 8) * (h // 8) * 3 * 64
+    assert lib.fds_sizes_packed(10, 64, 64, 0, None, None, None) == -1
+    key = bytes(16)
+    assert lib.fds_protect_image_packed(11, 8, 64, 64, 0, key, key, 1, 24, 32, None) == -1   # private not 16-aligned
+    assert lib.fds_protect_image_packed(11, 8, 64, 64, 0, key, key, 1, 32, None, None) == -1  # no scratch

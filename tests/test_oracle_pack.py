@@ -70,7 +70,7 @@ def _edges(w, h):
     return img.astype(np.uint8)
 
 
-@pytest.mark.parametrize("k", [0, 5])
+@pytest.mark.parametrize("k", [0, 5, 63])
 def test_eleven_bit_storage_is_lossless_eight_bit_is_not(k):
     img = _edges(64, 48)
     key, iv = synth.make_key(3), synth.make_iv(4)
