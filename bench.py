@@ -670,6 +670,71 @@ def compare_arm(args):
 
 
 # ------------------------------------------------------------------------------------------
+# bit-packed storage (Sect. 6.4.3, Table 5): protect / restore with 11-bit and 8-bit fields
+def packed_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_1512_02951_gb300 import api, build, synth
+
+    build.build()
+    api.init(0)
+    dev = torch.device("cuda", 0)
+    img = torch.from_numpy(synth.make_image(WIDTH, HEIGHT, IMG_SEED)).to(dev)
+    key, iv = synth.make_key(KEY_SEED), synth.make_iv(IV_SEED)
+    px_bytes = WIDTH * HEIGHT * 3
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)                                  # L2 flushed between timed launches
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    res = {}
+    pub16_b, priv16_b = api.sizes(WIDTH, HEIGHT, K_SEL)
+    pub16 = torch.empty((HEIGHT // 8, WIDTH // 8, 3, 63 - K_SEL), dtype=torch.int16, device=dev)
+    priv16 = torch.empty(priv16_b, dtype=torch.uint8, device=dev)
+    out = torch.empty_like(img)
+    res["int16"] = {"protect_ms": round(timed(lambda: api.protect_image(img, key, iv, K_SEL, pub16, priv16)), 5),
+                    "restore_ms": round(timed(lambda: api.restore_image(pub16, priv16, WIDTH, HEIGHT, K_SEL,
+                                                                         key, iv, out)), 5),
+                    "public_bytes": pub16_b, "private_bytes": priv16_b}
+    for form in (11, 8):
+        pub_b, priv_b, scr_b = api.sizes_packed(WIDTH, HEIGHT, K_SEL, form)
+        scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
+        pub = torch.empty(pub_b, dtype=torch.uint8, device=dev)
+        priv = torch.empty(max(priv_b, 16), dtype=torch.uint8, device=dev)
+        p_ms = timed(lambda: api.protect_image_packed(img, key, iv, K_SEL, form, scratch, pub, priv))
+        r_ms = timed(lambda: api.restore_image_packed(pub, priv[:priv_b], WIDTH, HEIGHT, K_SEL, key, iv, form,
+                                                      scratch, out))
+        res[f"packed{form}"] = {"protect_ms": round(p_ms, 5), "restore_ms": round(r_ms, 5),
+                                "public_bytes": pub_b, "private_bytes": priv_b,
+                                "stored_fraction_of_pixels": round((pub_b + priv_b) / px_bytes, 4),
+                                "private_fraction_of_pixels": round(priv_b / px_bytes, 4)}
+    p11 = res["packed11"]["protect_ms"]
+    line = {"metric": "protect throughput with 11-bit packed storage, MB/s of pixels",
+            "value": round(px_bytes / (p11 * 1e-3) / 1e6, 1), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": p11,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{WIDTH}x{HEIGHT} RGB uint8, k={K_SEL}: int16 vs 11-bit vs 8-bit "
+                                   "fragment storage", "l2": "256 MB buffer written between timed launches"},
+            "results": res,
+            "gpu_launches": args.steps * 14}   # int16 2 + 2 forms x (protect 3 + restore 3)
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # serving form: Poisson arrivals, mixed protect / restore, continuous batching
 SERVE_N, SERVE_RATE, SERVE_SEED = 1500, 500.0, 4242
 
@@ -735,7 +800,7 @@ def serve_arm(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["image4096", "precision", "compare", "batch2000", "serve"],
+    ap.add_argument("--workload", choices=["image4096", "precision", "compare", "batch2000", "serve", "packed"],
                     default="image4096")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -762,6 +827,8 @@ def main():
         batch_arm(args)
     elif args.workload == "serve":
         serve_arm(args)
+    elif args.workload == "packed":
+        packed_arm(args)
     else:
         gpu_arm(args)
 

@@ -239,10 +239,12 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
  * channel-blocks in [by][bx][c] order, each with its fields in fragment order (zigzag k+1..63,
  * resp. 0..k); the last byte is zero-padded.  The packed private stream is AES-128-CTR
  * encrypted from the IV like the int16 one.
- * fds_sizes_packed gives the packed fragment sizes and the device scratch the two calls need
- * (the int16 fragments and, for restore, the decrypted packed stream).  Arguments otherwise
- * as fds_protect_image / fds_restore_image; private and scratch 16-byte aligned, the packed
- * public fragment at any alignment.  scratch: device, owned by the caller, overwritten. */
+ * Protect is one launch (the transform packs and encrypts each tile in shared memory); restore
+ * decrypts, unpacks to int16 in scratch and runs the restore kernel.
+ * fds_sizes_packed gives the packed fragment sizes and the device scratch restore needs (the
+ * int16 fragments and the decrypted packed stream; protect does not touch scratch).  Arguments
+ * otherwise as fds_protect_image / fds_restore_image; private and scratch 16-byte aligned, the
+ * packed public fragment at any alignment.  scratch: device, owned by the caller, overwritten. */
 #define FDS_PACK_11 11
 #define FDS_PACK_8 8
 int fds_sizes_packed(int32_t form, int32_t width, int32_t height, int32_t k,

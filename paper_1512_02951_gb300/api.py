@@ -199,14 +199,18 @@ def sizes_packed(width: int, height: int, k: int, form: int = 11) -> tuple[int, 
 
 
 def protect_image_packed(pixels: torch.Tensor, key: bytes, iv: bytes, k: int, form: int = 11,
-                         scratch: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+                         scratch: torch.Tensor | None = None, public: torch.Tensor | None = None,
+                         private: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
     """fds_protect_image_packed: (packed public bytes, packed private ciphertext) as uint8
-    device tensors (11-bit or 8-bit storage)."""
+    device tensors (11-bit or 8-bit storage); `public` / `private` are optional output buffers
+    of at least the fds_sizes_packed byte counts."""
     w, h = _image_dims(pixels)
     pub_b, priv_b, scr_b = sizes_packed(w, h, k, form)
     dev = pixels.device
-    pub = torch.empty(max(pub_b, 1), dtype=torch.uint8, device=dev)
-    priv = torch.empty(max(priv_b, 16), dtype=torch.uint8, device=dev)
+    pub = torch.empty(max(pub_b, 1), dtype=torch.uint8, device=dev) if public is None else public
+    priv = torch.empty(max(priv_b, 16), dtype=torch.uint8, device=dev) if private is None else private
+    if pub.numel() < pub_b or priv.numel() < priv_b or pub.dtype != torch.uint8 or priv.dtype != torch.uint8:
+        raise ValueError("packed output buffers too small or not uint8")
     if scratch is None:
         scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
     rc = _lib.load().fds_protect_image_packed(form, pixels.data_ptr(), w, h, k, _check_key(key, "key"),
@@ -218,13 +222,16 @@ def protect_image_packed(pixels: torch.Tensor, key: bytes, iv: bytes, k: int, fo
 
 def restore_image_packed(public: torch.Tensor, private: torch.Tensor, width: int, height: int, k: int,
                          key: bytes, iv: bytes, form: int = 11,
-                         scratch: torch.Tensor | None = None) -> torch.Tensor:
-    """fds_restore_image_packed: the H x W x 3 uint8 image."""
+                         scratch: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_restore_image_packed: the H x W x 3 uint8 image (into `out` when given)."""
     dev = private.device
     _, _, scr_b = sizes_packed(width, height, k, form)
     if scratch is None:
         scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
-    out = torch.empty((height, width, 3), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = torch.empty((height, width, 3), dtype=torch.uint8, device=dev)
+    elif out.shape != (height, width, 3) or out.dtype != torch.uint8 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous H x W x 3 uint8 tensor")
     rc = _lib.load().fds_restore_image_packed(form, public.data_ptr() if public.numel() else None,
                                               private.data_ptr(), width, height, k, _check_key(key, "key"),
                                               _check_key(iv, "iv"), out.data_ptr(), scratch.data_ptr(),

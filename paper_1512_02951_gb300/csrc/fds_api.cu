@@ -557,25 +557,15 @@ int fds_protect_image_packed(int32_t form, const uint8_t* pixels, int32_t width,
   if (!key || !iv) return set_err(FDS_E_INVALID, "null pointer argument");
   int dev = 0;
   if ((rc = ensure_init(&dev))) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  int16_t* s_pub = static_cast<int16_t*>(scratch);
-  uint8_t* s_priv = static_cast<uint8_t*>(scratch) + align16u(pub16);
-  TileArgs a{};                                  // 1. the transform, private left in plaintext
+  TileArgs a{};                                  // one launch: transform, pack, encrypt
   a.pixels_in = pixels;
-  a.pub_out = s_pub;
-  a.priv_out = s_priv;
-  a.plain_private = 1;
+  a.pub_out = reinterpret_cast<int16_t*>(public_out);
+  a.priv_out = private_out;
+  a.pack = form;
   fill_geometry(a, width, height, k);
   expand_key(key, a.rk);
   iv_words(iv, &a.iv_hi, &a.iv_lo);
-  if ((rc = run_protect(a, dev, s, false))) return rc;
-  const long long ncb = 3ll * a.nblocks;         // 2. pack both fragments
-  cudaError_t e = launch_pack(s_pub, reinterpret_cast<const int16_t*>(s_priv), public_out, private_out, ncb, k,
-                              form, s);
-  if (e != cudaSuccess) return cuda_fail(e, "pack launch");
-  e = launch_aes_full(private_out, private_out, vpk, a.iv_hi, a.iv_lo, a.rk, g_tables[dev].T, s,
-                      g_tables[dev].sms);        // 3. encrypt the packed private stream
-  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "encryption launch");
+  return run_protect(a, dev, (cudaStream_t)stream, false);
 }
 
 int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8_t* private_in, int32_t width,

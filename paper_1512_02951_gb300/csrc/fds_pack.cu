@@ -1,12 +1,21 @@
-// Bit-packed coefficient storage (Sect. 6.4.3, Table 5): the paper's 11-bit storage (DC
-// unsigned in 11 bits, AC as a sign bit and a 10-bit magnitude) and 8-bit storage (AC as a
-// sign bit and a 7-bit magnitude, saturated), for both fragments.
+// Bit-packed coefficient storage (Sect. 6.4.3, Table 5), the unpacking direction: the
+// paper's 11-bit storage (DC unsigned in 11 bits, AC as a sign bit and a 10-bit magnitude) and
+// 8-bit storage (AC as a sign bit and a 7-bit magnitude) back to int16 fragments.  (Packing
+// happens inside the protect kernel.)
 //
 // A field of width w takes the next w bits of its stream, least significant bit first;
-// stream bit b is bit b % 8 of byte b / 8.  Channel-blocks follow each other in [by][bx][c]
-// order, each with its fields in fragment order.  Eight channel-blocks always end on a byte
-// boundary (8 w (63 - k) and 8 (11 + k w) bits), so one thread packs or unpacks a group of
-// eight channel-blocks and owns its bytes.
+// stream bit b is bit b % 8 of byte b / 8 (so, little-endian, bit b % 32 of 32-bit word
+// b / 32).  Channel-blocks follow each other in [by][bx][c] order, each with its fields in
+// fragment order; the last byte is padded with zero bits.
+//
+// An HBM-bound streaming pass, laid out so that every thread issues its loads up front:
+//   public stream  all fields have the AC width w, so 32 fields fill exactly w words: a
+//                  thread unpacks words [w t, w t + w) into fields [32 t, 32 t + 32), with
+//                  shifts fixed at compile time;
+//   private stream the period is 11 + k w bits per channel-block: one thread per
+//                  channel-block (its fields start at bit cb (11 + k w)).
+// One launch does both streams: the first blocks of the grid take the public stream, the
+// rest the private one.
 #include "fds_tile.cuh"
 
 namespace fds {
@@ -14,114 +23,117 @@ namespace fds {
 constexpr int kPackThreads = 256;
 constexpr int kDcBits = 11;
 
-// field code of value v: DC unsigned; AC sign-magnitude of width w (8-bit storage saturates)
-__device__ __forceinline__ uint32_t ac_code(int v, int w) {
-  const uint32_t mag_max = (1u << (w - 1)) - 1u;
-  uint32_t mag = (uint32_t)(v < 0 ? -v : v);
-  if (mag > mag_max) mag = mag_max;
-  return v < 0 ? ((1u << (w - 1)) | mag) : mag;
-}
-
 __device__ __forceinline__ int ac_value(uint32_t code, int w) {
   const int mag = (int)(code & ((1u << (w - 1)) - 1u));
   return (code >> (w - 1)) & 1u ? -mag : mag;
 }
 
-// Append a field to a byte stream: bits accumulate in acc (nbits of them), whole bytes go out.
-struct BitWriter {
-  uint8_t* out;
-  uint64_t acc;
-  int nbits;
-  __device__ __forceinline__ void put(uint32_t code, int w) {
-    acc |= (uint64_t)code << nbits;
-    nbits += w;
-    while (nbits >= 8) {
-      *out++ = (uint8_t)acc;
-      acc >>= 8;
-      nbits -= 8;
-    }
-  }
-  __device__ __forceinline__ void flush() {
-    if (nbits > 0) *out++ = (uint8_t)acc;
-    nbits = 0;
-  }
+// 32-bit word j of a byte stream of `nbytes` bytes (bytes past the end read as zero);
+// `aligned` = the stream's base is 4-byte aligned
+__device__ __forceinline__ uint32_t load_word(const uint8_t* in, long long j, long long nbytes, bool aligned) {
+  const long long b = 4 * j;
+  if (aligned && b + 4 <= nbytes) return *reinterpret_cast<const uint32_t*>(in + b);
+  uint32_t v = 0;
+  for (int q = 0; q < 4; ++q)
+    if (b + q < nbytes) v |= (uint32_t)in[b + q] << (8 * q);
+  return v;
+}
+
+struct PackArgs {
+  const uint8_t* pub;     // packed public stream, pub_bytes
+  const uint8_t* priv;    // packed private stream, priv_bytes
+  long long nfields;      // ncb (63 - k)
+  long long ncb;
+  long long pub_bytes, priv_bytes;
+  int k;
+  int pub_blocks;         // blocks [0, pub_blocks) take the public stream
+  bool pub_aligned, priv_aligned;
 };
 
-struct BitReader {
-  const uint8_t* in;
-  uint64_t acc;
-  int nbits;
-  __device__ __forceinline__ uint32_t get(int w) {
-    while (nbits < w) {
-      acc |= (uint64_t)(*in++) << nbits;
-      nbits += 8;
+template <int W>
+__device__ __forceinline__ void unpack_public(const PackArgs& a, long long t, int16_t* pub16) {
+  const long long f0 = 32 * t;
+  if (f0 >= a.nfields) return;
+  uint32_t word[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) word[j] = load_word(a.pub, W * t + j, a.pub_bytes, a.pub_aligned);
+  int v[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int b = W * i;
+    uint32_t c = word[b >> 5] >> (b & 31);
+    if ((b & 31) + W > 32) c |= word[(b >> 5) + 1] << (32 - (b & 31));
+    v[i] = ac_value(c & ((1u << W) - 1u), W);
+  }
+  if (f0 + 32 <= a.nfields) {
+    uint4* dst = reinterpret_cast<uint4*>(pub16 + f0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t u[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        u[m] = ((uint32_t)v[8 * q + 2 * m] & 0xffffu) | ((uint32_t)v[8 * q + 2 * m + 1] << 16);
+      dst[q] = make_uint4(u[0], u[1], u[2], u[3]);
     }
-    const uint32_t code = (uint32_t)(acc & ((1ull << w) - 1ull));
-    acc >>= w;
-    nbits -= w;
-    return code;
-  }
-};
-
-// int16 fragments ([ncb][63 - k] public, [ncb][k + 1] private plaintext) -> packed streams
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(const int16_t* pub16, const int16_t* priv16,
-                                                            uint8_t* pub_out, uint8_t* priv_out, long long ncb,
-                                                            int k, int w) {
-  const long long g = (long long)blockIdx.x * kPackThreads + threadIdx.x;
-  const long long c0 = 8 * g;
-  if (c0 >= ncb) return;
-  const int n = (int)min(8ll, ncb - c0);
-  const int npub = 63 - k;
-  if (npub > 0) {
-    BitWriter bw{pub_out + g * (long long)(npub * w), 0, 0};
-    const int16_t* src = pub16 + c0 * npub;
-    for (int i = 0; i < n * npub; ++i) bw.put(ac_code(src[i], w), w);
-    bw.flush();
-  }
-  BitWriter bv{priv_out + g * (long long)(kDcBits + k * w), 0, 0};
-  const int16_t* src = priv16 + c0 * (k + 1);
-  for (int c = 0; c < n; ++c) {
-    bv.put((uint32_t)src[c * (k + 1)] & 0x7ffu, kDcBits);
-    for (int z = 1; z <= k; ++z) bv.put(ac_code(src[c * (k + 1) + z], w), w);
-  }
-  bv.flush();
-}
-
-// packed streams -> int16 fragments
-__global__ void __launch_bounds__(kPackThreads) unpack_kernel(const uint8_t* pub_in, const uint8_t* priv_in,
-                                                              int16_t* pub16, int16_t* priv16, long long ncb, int k,
-                                                              int w) {
-  const long long g = (long long)blockIdx.x * kPackThreads + threadIdx.x;
-  const long long c0 = 8 * g;
-  if (c0 >= ncb) return;
-  const int n = (int)min(8ll, ncb - c0);
-  const int npub = 63 - k;
-  if (npub > 0) {
-    BitReader br{pub_in + g * (long long)(npub * w), 0, 0};
-    int16_t* dst = pub16 + c0 * npub;
-    for (int i = 0; i < n * npub; ++i) dst[i] = (int16_t)ac_value(br.get(w), w);
-  }
-  BitReader bv{priv_in + g * (long long)(kDcBits + k * w), 0, 0};
-  int16_t* dst = priv16 + c0 * (k + 1);
-  for (int c = 0; c < n; ++c) {
-    dst[c * (k + 1)] = (int16_t)bv.get(kDcBits);
-    for (int z = 1; z <= k; ++z) dst[c * (k + 1) + z] = (int16_t)ac_value(bv.get(w), w);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (f0 + i < a.nfields) pub16[f0 + i] = (int16_t)v[i];
   }
 }
 
-cudaError_t launch_pack(const int16_t* pub16, const int16_t* priv16, uint8_t* pub_out, uint8_t* priv_out,
-                        long long ncb, int k, int w, cudaStream_t s) {
-  const long long groups = (ncb + 7) / 8;
-  const unsigned grid = (unsigned)((groups + kPackThreads - 1) / kPackThreads);
-  if (grid) pack_kernel<<<grid, kPackThreads, 0, s>>>(pub16, priv16, pub_out, priv_out, ncb, k, w);
-  return cudaGetLastError();
+// private: thread per channel-block; its fields start at bit cb (11 + k w)
+__device__ __forceinline__ void unpack_private(const PackArgs& a, long long cb, int w, int16_t* priv16) {
+  if (cb >= a.ncb) return;
+  const long long period = kDcBits + (long long)a.k * w;
+  long long pos = cb * period;
+  int16_t* dst = priv16 + cb * (a.k + 1);
+  for (int z = 0; z <= a.k; ++z) {
+    const int fw = z == 0 ? kDcBits : w;
+    const long long j = pos >> 5;
+    const int sh = (int)(pos & 31);
+    uint64_t x = load_word(a.priv, j, a.priv_bytes, a.priv_aligned);
+    if (sh + fw > 32) x |= (uint64_t)load_word(a.priv, j + 1, a.priv_bytes, a.priv_aligned) << 32;
+    const uint32_t c = (uint32_t)(x >> sh) & ((1u << fw) - 1u);
+    dst[z] = (int16_t)(z == 0 ? (int)c : ac_value(c, w));
+    pos += fw;
+  }
 }
 
+template <int W>
+__global__ void __launch_bounds__(kPackThreads) unpack_kernel(const __grid_constant__ PackArgs a, int16_t* pub16,
+                                                              int16_t* priv16) {
+  if ((int)blockIdx.x < a.pub_blocks)
+    unpack_public<W>(a, (long long)blockIdx.x * kPackThreads + threadIdx.x, pub16);
+  else
+    unpack_private(a, (long long)(blockIdx.x - a.pub_blocks) * kPackThreads + threadIdx.x, W, priv16);
+}
+
+static PackArgs pack_args(const uint8_t* pub, const uint8_t* priv, long long ncb, int k, int w) {
+  PackArgs a{};
+  a.pub = pub;
+  a.priv = priv;
+  a.ncb = ncb;
+  a.k = k;
+  a.nfields = ncb * (63 - k);
+  a.pub_bytes = (a.nfields * w + 7) / 8;
+  a.priv_bytes = (ncb * (kDcBits + (long long)k * w) + 7) / 8;
+  a.pub_aligned = (reinterpret_cast<uintptr_t>(pub) & 3) == 0;
+  a.priv_aligned = (reinterpret_cast<uintptr_t>(priv) & 3) == 0;
+  a.pub_blocks = (int)((a.nfields + 32ll * kPackThreads - 1) / (32ll * kPackThreads));
+  return a;
+}
+
+// packed streams -> int16 fragments (pub16 16-byte aligned)
 cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
                           long long ncb, int k, int w, cudaStream_t s) {
-  const long long groups = (ncb + 7) / 8;
-  const unsigned grid = (unsigned)((groups + kPackThreads - 1) / kPackThreads);
-  if (grid) unpack_kernel<<<grid, kPackThreads, 0, s>>>(pub_in, priv_in, pub16, priv16, ncb, k, w);
+  const PackArgs a = pack_args(pub_in, priv_in, ncb, k, w);
+  const long long grid = a.pub_blocks + (ncb + kPackThreads - 1) / kPackThreads;
+  if (grid == 0) return cudaSuccess;
+  if (w == 11)
+    unpack_kernel<11><<<(unsigned)grid, kPackThreads, 0, s>>>(a, pub16, priv16);
+  else
+    unpack_kernel<8><<<(unsigned)grid, kPackThreads, 0, s>>>(a, pub16, priv16);
   return cudaGetLastError();
 }
 

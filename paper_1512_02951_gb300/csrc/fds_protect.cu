@@ -14,6 +14,13 @@
 //      staging area, one thread per 16-byte keystream block
 // One staging area (so that three CTAs fit on an SM): the previous tile's bulk stores must
 // have read it before the transform writes it again.
+//
+// Packed storage (Sect. 6.4.3, Table 5; PACK = 11 or 8 bits per AC field): after step 2 the
+// staging area is packed in place into the tile's part of the two bit streams (DC unsigned in
+// 11 bits, AC sign-magnitude in PACK bits, least significant bit first, channel-blocks in
+// stream order), and AES-128-CTR runs over the packed private bytes at their offset in the
+// image's private stream.  A full tile holds 192 channel-blocks, a multiple of 8, so every
+// tile's part of either stream starts on a byte boundary.
 #include "fds_tile.cuh"
 
 namespace fds {
@@ -50,6 +57,179 @@ __device__ __forceinline__ void store_private(const TileSlot* sl, const uint8_t*
     *reinterpret_cast<uint16_t*>(vdst + j) = *reinterpret_cast<const uint16_t*>(vsrc + j);
 }
 
+// ---- packed storage ---------------------------------------------------------------------
+constexpr int kDcBits = 11;
+
+// field code of AC value v in W bits: sign-magnitude, the magnitude saturated to W - 1 bits
+template <int W>
+__device__ __forceinline__ uint32_t ac_code(int v) {
+  const uint32_t mag_max = (1u << (W - 1)) - 1u;
+  uint32_t mag = (uint32_t)(v < 0 ? -v : v);
+  if (mag > mag_max) mag = mag_max;
+  return v < 0 ? ((1u << (W - 1)) | mag) : mag;
+}
+
+// Pack the staged tile in place (all threads; contains barriers, so every thread calls it).
+// Public: fields f (stream order, int16 at st + 2 f) in groups of 32; group g fills words
+// [W g, W g + W) of the packed public part at st.  Private: word j of the packed private part
+// (at the private staging offset) gathers the fields overlapping bits [32 j, 32 j + 32); a
+// channel-block takes 11 + k W bits.  Each round reads its inputs into registers, waits at a
+// barrier and writes; the words a round writes lie below every input a later round reads
+// (a word of 32 bits holds at least 2.9 fields of at most 11 bits, which took 5.8 bytes as
+// int16), and the packed public part ends below the private staging offset (W <= 11 < 16).
+template <int W>
+__device__ __forceinline__ void pack_tile(uint8_t* st, int nb, int k) {
+  const int t = threadIdx.x;
+  const int npub = 63 - k;
+  const int nf = 3 * nb * npub;
+  const int ngroups = (nf + 31) >> 5;
+  const int period = kDcBits + k * W;
+  const int pbits = 3 * nb * period;
+  const int nwords = (pbits + 31) >> 5;
+  const int16_t* pub16 = reinterpret_cast<const int16_t*>(st);
+  uint32_t* pubw = reinterpret_cast<uint32_t*>(st);
+  uint8_t* pv = st + kTileCb * 2 * npub;
+  const int16_t* priv16 = reinterpret_cast<const int16_t*>(pv);
+  uint32_t* privw = reinterpret_cast<uint32_t*>(pv);
+  const int nrounds = ngroups > nwords ? ngroups : nwords;
+  for (int r0 = 0; r0 < nrounds; r0 += kThreads) {
+    const int g = r0 + t;
+    uint32_t pw[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) pw[j] = 0;
+    if (g < ngroups) {
+      const int f0 = 32 * g;
+      int v[32];
+      if (f0 + 32 <= nf) {
+        const uint4* src = reinterpret_cast<const uint4*>(pub16 + f0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 x = src[q];
+          const uint32_t u[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            v[8 * q + 2 * m] = (int16_t)(u[m] & 0xffffu);
+            v[8 * q + 2 * m + 1] = (int16_t)(u[m] >> 16);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = f0 + i < nf ? pub16[f0 + i] : 0;   // zero padding
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const uint32_t c = ac_code<W>(v[i]);
+        const int b = W * i;
+        pw[b >> 5] |= c << (b & 31);
+        if ((b & 31) + W > 32) pw[(b >> 5) + 1] |= c >> (32 - (b & 31));
+      }
+    }
+    uint32_t vw = 0;
+    if (g < nwords) {
+      const int bit = 32 * g;
+      const int end = bit + 32 < pbits ? bit + 32 : pbits;
+      int cb = bit / period;
+      const int r = bit - cb * period;
+      int z = r < kDcBits ? 0 : 1 + (r - kDcBits) / W;
+      int pos = cb * period + (z == 0 ? 0 : kDcBits + (z - 1) * W);
+      while (pos < end) {
+        const int v = priv16[cb * (k + 1) + z];
+        const uint32_t c = z == 0 ? ((uint32_t)v & 0x7ffu) : ac_code<W>(v);
+        const int sh = pos - bit;   // in (-11, 32)
+        vw |= sh >= 0 ? c << sh : c >> (-sh);
+        pos += z == 0 ? kDcBits : W;
+        if (++z > k) {
+          z = 0;
+          ++cb;
+        }
+      }
+    }
+    __syncthreads();
+    if (g < ngroups) {
+      if constexpr (W == 8) {
+        uint4* d = reinterpret_cast<uint4*>(pubw + W * g);
+        d[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+        d[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) pubw[W * g + j] = pw[j];
+      }
+    }
+    if (g < nwords) privw[g] = vw;
+  }
+}
+
+// bytes of a tile's packed public / private part and their offsets in the image's streams
+// (a full tile: 24 (63 - k) W and 24 (11 + k W) bytes)
+template <int W>
+__device__ __forceinline__ void packed_extent(const TileSlot* sl, bool priv, uint64_t& off, int& bytes) {
+  const int k = sl->k;
+  const int per_cb = priv ? kDcBits + k * W : (63 - k) * W;   // bits per channel-block
+  off = (uint64_t)sl->local * 24ull * (uint64_t)per_cb;
+  bytes = (3 * sl->nb * per_cb + 7) >> 3;
+}
+
+// the packed public part of slot sl (at st) to global memory (all threads): one bulk store
+// when its destination is 16-byte aligned, else 4-byte or byte stores
+template <int W>
+__device__ __forceinline__ void store_public_packed(const TileSlot* sl, const uint8_t* st) {
+  const int t = threadIdx.x;
+  uint64_t off;
+  int bytes;
+  packed_extent<W>(sl, false, off, bytes);
+  uint8_t* dst = sl->pub_out + off;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(dst);
+  if ((al & 15) == 0) {
+    if (t == 0 && (bytes >> 4)) {
+      bulk_store(dst, st, (uint32_t)(bytes & ~15));
+      bulk_commit();
+    }
+    if (t < (bytes & 15)) dst[(bytes & ~15) + t] = st[(bytes & ~15) + t];
+  } else if ((al & 3) == 0) {
+    for (int i = t; i < (bytes >> 2); i += kThreads)
+      reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(st)[i];
+    if (t < (bytes & 3)) dst[(bytes & ~3) + t] = st[(bytes & ~3) + t];
+  } else {
+    for (int i = t; i < bytes; i += kThreads) dst[i] = st[i];
+  }
+}
+
+// the packed (encrypted) private part of slot sl to global memory (all threads); the private
+// stream is 16-byte aligned and a tile's offset is a multiple of 8
+template <int W>
+__device__ __forceinline__ void store_private_packed(const TileSlot* sl, const uint8_t* st) {
+  const int t = threadIdx.x;
+  uint64_t off;
+  int bytes;
+  packed_extent<W>(sl, true, off, bytes);
+  uint8_t* dst = sl->priv_out + off;
+  const uint8_t* src = st + kTileCb * 2 * (63 - sl->k);
+  for (int i = t; i < (bytes >> 2); i += kThreads)
+    reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
+  if (t < (bytes & 3)) dst[(bytes & ~3) + t] = src[(bytes & ~3) + t];
+}
+
+// AES-128-CTR over the tile's packed private part (words at w, stream bytes [off, off +
+// bytes), off a multiple of 4): one thread per keystream block the part overlaps; a block
+// that straddles two tiles is generated by both, each XORing its own words
+__device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int bytes, const TileSlot* sl,
+                                                const uint32_t* rk, const uint32_t* Ts) {
+  const uint64_t b0 = off >> 4;
+  const int nblk = (int)(((off + (uint64_t)bytes + 15) >> 4) - b0);
+  const int nw = (bytes + 3) >> 2;
+  const int skew = (int)((off & 15) >> 2);
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+    uint32_t s[4];
+    ctr_block(sl->iv_hi, sl->iv_lo, b0 + i, s);
+    aes128_encrypt(s, rk, Ts);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int wi = 4 * i + m - skew;
+      if (wi >= 0 && wi < nw) w[wi] ^= s[m];
+    }
+  }
+}
+
 // cp.async the pixels of slot sl into pixel tile pix (all threads)
 __device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
   const uint64_t w3 = (uint64_t)sl->width * 3ull;
@@ -63,8 +243,9 @@ __device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
 }
 
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
-// from the kernel parameters, which AES then takes as constant-bank operands)
-template <int K, bool DEBUG, bool BATCH>
+// from the kernel parameters, which AES then takes as constant-bank operands).
+// PACK: 0 = int16 fragments; 11 or 8 = packed streams (one image)
+template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
@@ -100,7 +281,10 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     if (t == 0) misc[0] = 0;
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
-    if (!DEBUG && t == 0 && have_prev) {
+    if constexpr (PACK != 0) {
+      if (have_prev) store_private_packed<PACK>(slot(s_prev), smem + kSmemStage);
+      if (t == 0) bulk_wait_read_all();      // the staging area may be written again
+    } else if (!DEBUG && t == 0 && have_prev) {
       store_private(slot(s_prev), smem + kSmemStage);   // the public part left before its AES
       bulk_wait_read_all();                  // the staging area may be written again
     }
@@ -237,20 +421,35 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
       if (fail) atomicAdd(&misc[3], 1);
       if (t == 0) misc[1] += misc[0];
     }
+    if constexpr (PACK != 0) {
+      __syncthreads();                                 // every staged coefficient is final
+      pack_tile<PACK>(smem + kSmemStage, nb, k);
+    }
     fence_proxy_async();                   // every thread's staging writes, before the bulk store
     __syncthreads();                                                       // C
-    if (t == 0) store_public(sl, smem + kSmemStage);   // final: it leaves during the AES
-    if (!a.plain_private)
-      ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
-               ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
-               BATCH ? sl->rk : a.rk, Ts);
+    if constexpr (PACK != 0) {
+      store_public_packed<PACK>(sl, smem + kSmemStage);   // it leaves during the AES
+      uint64_t off;
+      int bytes;
+      packed_extent<PACK>(sl, true, off, bytes);
+      ctr_tile_packed(reinterpret_cast<uint32_t*>(privst), off, bytes, sl, a.rk, Ts);
+    } else {
+      if (t == 0) store_public(sl, smem + kSmemStage);   // final: it leaves during the AES
+      if (!a.plain_private)
+        ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
+                 ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
+                 BATCH ? sl->rk : a.rk, Ts);
+    }
     fence_proxy_async();
     have_prev = true;
   }
   if (DEBUG) return;
   __syncthreads();
+  if constexpr (PACK != 0) {
+    if (have_prev) store_private_packed<PACK>(slot((it + 2) % 3), smem + kSmemStage);
+  }
   if (t == 0) {
-    if (have_prev) store_private(slot((it + 2) % 3), smem + kSmemStage);
+    if (PACK == 0 && have_prev) store_private(slot((it + 2) % 3), smem + kSmemStage);
     bulk_wait_all();
     if (a.counters) {
       if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
@@ -260,20 +459,28 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
   }
 }
 
-template <int K, bool DEBUG, bool BATCH>
+template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
-  cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH>, kSmemBytes, attr);
+  cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, kSmemBytes, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
   const int cap = (per_sm == 1 ? 1 : kPCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
-  if (grid > 0) protect_kernel<K, DEBUG, BATCH><<<grid, kThreads, kSmemBytes, s>>>(a);
+  if (grid > 0) protect_kernel<K, DEBUG, BATCH, PACK><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
-// k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile
+// k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile;
+// a.pack (11 or 8: packed streams) is for one image
 cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm) {
+  if (a.pack) {
+    if (debug || a.images || a.k < 0 || (a.pack != 11 && a.pack != 8)) return cudaErrorInvalidValue;
+    if (a.pack == 11) return a.k == 5 ? launch_k<5, false, false, 11>(a, s, sms, per_sm)
+                                      : launch_k<-1, false, false, 11>(a, s, sms, per_sm);
+    return a.k == 5 ? launch_k<5, false, false, 8>(a, s, sms, per_sm)
+                    : launch_k<-1, false, false, 8>(a, s, sms, per_sm);
+  }
   if (debug) return launch_k<-1, true, false>(a, s, sms, per_sm);
   if (a.images) {
     if (a.k == 0) return launch_k<0, false, true>(a, s, sms, per_sm);

@@ -90,6 +90,9 @@ struct TileArgs {
   // nonzero: the private fragment stays in plaintext (protect does not encrypt it, restore
   // does not decrypt it); the packed-storage entry points encrypt the packed stream instead
   int32_t plain_private;
+  // protect of one image into packed streams: 11 or 8 bits per AC field (pub_out / priv_out
+  // then point to the packed public stream and the packed private stream); 0 = int16
+  int32_t pack;
 };
 
 // What a CTA knows about the tile it is working on (shared memory, filled one tile ahead).
@@ -113,9 +116,7 @@ cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_s
 // AES-128-CTR over a whole buffer (the full-encryption comparator)
 cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
                             const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms);
-// bit-packed storage: int16 fragments <-> packed streams, w = 11 or 8 bits per AC field
-cudaError_t launch_pack(const int16_t* pub16, const int16_t* priv16, uint8_t* pub_out, uint8_t* priv_out,
-                        long long ncb, int k, int w, cudaStream_t s);
+// bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
 cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
                           long long ncb, int k, int w, cudaStream_t s);
 // tensor-core protect of one image (form 0: BF16 three limbs, 1: TF32 two limbs); tiles of

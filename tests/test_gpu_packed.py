@@ -52,3 +52,24 @@ def test_packed_matches_oracle(api, form, w, h, k):
 def test_packed_high_contrast_and_512(api, form):
     _check(api, _edges(64, 48), 5, form, seed=1)          # AC up to 924: 8-bit storage saturates
     _check(api, synth.make_image(512, 512, 1), 5, form, seed=2)
+
+
+@pytest.mark.parametrize("form", [11, 8])
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_packed_public_at_any_alignment(api, form, offset):
+    # the packed public fragment may start at any byte; the result is the same bytes
+    w, h, k = 136, 72, 5
+    img = synth.make_image(w, h, 77)
+    key, iv = synth.make_key(71), synth.make_iv(72)
+    pub_b, priv_b, _ = api.sizes_packed(w, h, k, form)
+    buf = torch.zeros(pub_b + 8, dtype=torch.uint8, device=DEV)
+    pub = buf[offset:offset + pub_b]
+    api.protect_image_packed(torch.from_numpy(img).to(DEV), key, iv, k, form, public=pub,
+                             private=torch.empty(priv_b, dtype=torch.uint8, device=DEV))
+    want_pub, want_priv = pack.protect_packed(img, key, iv, k, form)
+    got = buf.cpu().numpy()
+    assert got[offset:offset + pub_b].tobytes() == want_pub
+    assert not got[:offset].any() and not got[offset + pub_b:].any()      # nothing written outside
+    priv = torch.from_numpy(np.frombuffer(want_priv, dtype=np.uint8).copy()).to(DEV)
+    back = api.restore_image_packed(pub, priv, w, h, k, key, iv, form).cpu().numpy()
+    assert np.array_equal(back, pack.restore_packed(want_pub, want_priv, key, iv, k, form, w, h))
