@@ -258,6 +258,29 @@ int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8
                              const uint8_t iv[16], uint8_t* pixels_out, void* scratch,
                              void* stream);
 
+/* The paper's own form of the public fragment (Sect. 6.5.1, Fig. 10; Fig. 7 (b)): the public
+ * coefficients as an image.  Per channel-block the zigzag positions 1..k are zero and the DC
+ * coefficient is 1024 (= 8 x 128: the zero-mean block shifted to mid-grey), the positions
+ * k+1..63 come from the int16 public fragment; the exact inverse DCT is rounded half away
+ * from zero and clamped to [0, 255], as in restore.  The public coefficients come back from
+ * such an image through fds_protect_image's public output (a constant shift changes only the
+ * private DC coefficient).
+ * public_in: device int16 [H/8][W/8][3][63-k] (16-byte aligned; may be null when k = 63);
+ * image_out: device H x W x 3 uint8 (8-byte aligned), written.  No key: nothing private. */
+int fds_public_image(const int16_t* public_in, int32_t width, int32_t height, int32_t k,
+                     uint8_t* image_out, void* stream);
+
+/* Statistics used to judge protected images (Sect. 6.6): the per-channel histogram (6.6.1) and
+ * exact integer sums for the correlation coefficient of adjacent pixels (6.6.2), over every
+ * pair of a pixel and its right, lower and lower-right neighbour:
+ *   r = (n Sxy - Sx Sy) / sqrt((n Sxx - Sx^2)(n Syy - Sy^2)).
+ * image: device H x W x 3 uint8, any W, H >= 1.  histogram_out: device uint64 [3][256]
+ * (channel, level); pair_sums_out: device int64 [3][3][6] = [direction: right, down,
+ * down-right][channel][n, Sx, Sy, Sxx, Syy, Sxy].  Both 8-byte aligned and overwritten
+ * (cleared on `stream`, then accumulated). */
+int fds_image_stats(const uint8_t* image, int32_t width, int32_t height, uint64_t* histogram_out,
+                    int64_t* pair_sums_out, void* stream);
+
 /* Diagnostics (host only, no device needed): the tensor-core form's B operand as the kernel
  * holds it in shared memory -- row n = 64 l + 8u + v is limb l of the basis function
  * (u, v), K index 8y + x, 128-byte rows, 16-byte chunk c of row n stored at chunk c ^ (n & 7);

@@ -6,6 +6,7 @@ restore runs in the library's CUDA kernels.  Function names follow include/fds.h
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass
 from typing import Sequence
 
@@ -237,6 +238,52 @@ def restore_image_packed(public: torch.Tensor, private: torch.Tensor, width: int
                                               _check_key(iv, "iv"), out.data_ptr(), scratch.data_ptr(),
                                               _stream_ptr(dev))
     _lib.check(rc, "fds_restore_image_packed")
+    return out
+
+
+def public_image(public: torch.Tensor, width: int, height: int, k: int,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_public_image: the paper-form public fragment, an H x W x 3 uint8 image (private
+    zigzag positions zero, DC 1024, exact inverse DCT, rounded and clamped)."""
+    dev = public.device
+    if out is None:
+        out = torch.empty((height, width, 3), dtype=torch.uint8, device=dev)
+    elif out.shape != (height, width, 3) or out.dtype != torch.uint8 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous H x W x 3 uint8 tensor")
+    if public.numel() and (public.dtype != torch.int16 or not public.is_contiguous()):
+        raise ValueError("public must be a contiguous int16 tensor")
+    rc = _lib.load().fds_public_image(public.data_ptr() if public.numel() else None, width, height, k,
+                                      out.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_public_image")
+    return out
+
+
+def image_stats(image: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    """fds_image_stats: (histogram uint64-as-int64 [3, 256], pair sums int64 [3, 3, 6]) as
+    device tensors; see correlation() for r."""
+    if image.dtype != torch.uint8 or image.dim() != 3 or image.shape[2] != 3 or not image.is_contiguous():
+        raise ValueError("image must be a contiguous H x W x 3 uint8 tensor")
+    h, w, _ = image.shape
+    hist = torch.empty((3, 256), dtype=torch.int64, device=image.device)
+    sums = torch.empty((3, 3, 6), dtype=torch.int64, device=image.device)
+    rc = _lib.load().fds_image_stats(image.data_ptr(), w, h, hist.data_ptr(), sums.data_ptr(),
+                                     _stream_ptr(image.device))
+    _lib.check(rc, "fds_image_stats")
+    return hist, sums
+
+
+def correlation(sums) -> list:
+    """Correlation coefficients r [direction][channel] (right, down, down-right) from the exact
+    pair sums of image_stats (Sect. 6.6.2); None where a variance is zero."""
+    s = sums.tolist() if hasattr(sums, "tolist") else sums
+    out = []
+    for d in range(3):
+        row = []
+        for c in range(3):
+            n, sx, sy, sxx, syy, sxy = (int(v) for v in s[d][c])
+            dx, dy = n * sxx - sx * sx, n * syy - sy * sy
+            row.append((n * sxy - sx * sy) / math.sqrt(dx * dy) if dx > 0 and dy > 0 else None)
+        out.append(row)
     return out
 
 

@@ -603,6 +603,43 @@ int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8
   return run_restore(a, dev, s);
 }
 
+// ---- the paper-form public fragment and the statistics of Sect. 6.6
+int fds_public_image(const int16_t* public_in, int32_t width, int32_t height, int32_t k, uint8_t* image_out,
+                     void* stream) {
+  if (bad_dims(width, height)) return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8");
+  if (k < 0 || k > 63) return set_err(FDS_E_INVALID, "k must be in 0..63");
+  if (!image_out || (k < 63 && !public_in)) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(image_out, 8) || misaligned(public_in, 16))
+    return set_err(FDS_E_INVALID, "image must be 8-byte aligned, the fragment 16-byte aligned");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  TileArgs a{};
+  a.pub_in = public_in;
+  a.pixels_out = image_out;
+  a.public_image = 1;
+  fill_geometry(a, width, height, k);
+  return run_restore(a, dev, (cudaStream_t)stream);
+}
+
+int fds_image_stats(const uint8_t* image, int32_t width, int32_t height, uint64_t* histogram_out,
+                    int64_t* pair_sums_out, void* stream) {
+  if (width <= 0 || height <= 0) return set_err(FDS_E_INVALID, "width and height must be positive");
+  if (!image || !histogram_out || !pair_sums_out) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(histogram_out, 8) || misaligned(pair_sums_out, 8))
+    return set_err(FDS_E_INVALID, "outputs must be 8-byte aligned");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(histogram_out, 0, 3 * 256 * sizeof(uint64_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pair_sums_out, 0, 3 * 3 * 6 * sizeof(int64_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the statistics");
+  e = launch_image_stats(image, width, height, reinterpret_cast<unsigned long long*>(histogram_out),
+                         reinterpret_cast<long long*>(pair_sums_out), s, g_tables[dev].sms);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "statistics launch");
+}
+
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {
   if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
   std::vector<uint8_t> img;

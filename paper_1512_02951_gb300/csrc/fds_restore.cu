@@ -15,6 +15,11 @@
 //   C. 3. the pixel tile goes to global memory: one bulk (TMA engine) store per pixel row when
 //      the tile's rows are contiguous and 16-byte aligned, else 8-byte stores.  The pixel tile
 //      is double-buffered so the bulk stores overlap the next tile.
+//
+// Public-image form (PUBIMG; the paper's public fragment as an image, Sect. 6.5.1 Fig. 10):
+// the same kernel with the private positions "padded with zeros" -- the private staging
+// holds the constant (1024, 0, .., 0) per channel-block (DC 8 x 128: the zero-mean block
+// shifted to mid-grey), nothing private is loaded or decrypted.
 #include "fds_tile.cuh"
 
 namespace fds {
@@ -44,24 +49,27 @@ __device__ __forceinline__ void gather_coefs(const int16_t* pubst, const int16_t
 // cp.async the public and private ranges of slot sl's tile into staging area st
 // True if both fragment ranges of the tile are whole 16-byte units (then each arrives as one
 // bulk copy completing on an mbarrier; else as 16-byte cp.async pieces)
+// PUB_ONLY: the public range alone
+template <bool PUB_ONLY = false>
 __device__ __forceinline__ bool frag_bulk(const TileSlot* sl) {
   const int k = sl->k, nb = sl->nb;
-  return ((nb * 6 * (63 - k)) & 15) == 0 && ((nb * 6 * (k + 1)) & 15) == 0;
+  return ((nb * 6 * (63 - k)) & 15) == 0 && (PUB_ONLY || ((nb * 6 * (k + 1)) & 15) == 0);
 }
 // Load the public and private ranges of slot sl's tile into staging area st (all threads call
 // it; thread 0 issues the bulk copies)
+template <bool PUB_ONLY = false>
 __device__ __forceinline__ void load_fragments(const TileSlot* sl, uint8_t* st, uint64_t* bar) {
   const int t = threadIdx.x;
   const int k = sl->k, npub = 63 - k, nb = sl->nb;
-  const int pub_bytes = nb * 6 * npub, priv_bytes = nb * 6 * (k + 1);
+  const int pub_bytes = nb * 6 * npub, priv_bytes = PUB_ONLY ? 0 : nb * 6 * (k + 1);
   const uint8_t* psrc = sl->pub_in + (uint64_t)sl->local * kTileBlocks * 6ull * npub;
   const uint8_t* vsrc = sl->priv_in + (uint64_t)sl->local * kTileBlocks * 6ull * (k + 1);
   uint8_t* vdst = st + kTileCb * 2 * npub;
-  if (frag_bulk(sl)) {
+  if (frag_bulk<PUB_ONLY>(sl)) {
     if (t == 0) {
       mbar_expect_tx(bar, (uint32_t)(pub_bytes + priv_bytes));
       if (pub_bytes) bulk_load(st, psrc, (uint32_t)pub_bytes, bar);
-      bulk_load(vdst, vsrc, (uint32_t)priv_bytes, bar);
+      if (priv_bytes) bulk_load(vdst, vsrc, (uint32_t)priv_bytes, bar);
     }
     return;
   }
@@ -80,8 +88,9 @@ __device__ __forceinline__ void load_fragments(const TileSlot* sl, uint8_t* st, 
 }
 // Wait until this thread may read what load_fragments loaded (a barrier must follow);
 // phase: the next phase of bar; lost counts bulk loads that did not complete in time
+template <bool PUB_ONLY = false>
 __device__ __forceinline__ void wait_fragments(const TileSlot* sl, uint64_t* bar, uint32_t& phase, int& lost) {
-  if (frag_bulk(sl)) {
+  if (frag_bulk<PUB_ONLY>(sl)) {
     if (!mbar_wait(bar, phase)) ++lost;
     phase ^= 1u;
   } else {
@@ -99,7 +108,7 @@ __device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint
 
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
 // from the kernel parameters, which AES then takes as constant-bank operands)
-template <int K, bool BATCH>
+template <int K, bool BATCH, bool PUBIMG = false>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) uint32_t Ts[1024];                // AES T-tables
@@ -128,11 +137,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     mbar_init(bars + 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if constexpr (PUBIMG) {   // the private staging of both areas: (1024, 0, .., 0) per channel-block
+    const int kk = a.k, np = kTileCb * (kk + 1);
+    for (int i = t; i < 2 * np; i += kThreads) {
+      const int j = i < np ? i : i - np;
+      reinterpret_cast<int16_t*>(stage(i < np ? 0 : 1) + kTileCb * 2 * (63 - kk))[j] =
+          (int16_t)(j % (kk + 1) == 0 ? 1024 : 0);
+    }
+  }
   __syncthreads();
-  load_fragments(slot(0), stage(0), bars);
-  wait_fragments(slot(0), bars, phase[0], lost);
+  load_fragments<PUBIMG>(slot(0), stage(0), bars);
+  wait_fragments<PUBIMG>(slot(0), bars, phase[0], lost);
   __syncthreads();
-  if (!a.plain_private) decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
+  if (!PUBIMG && !a.plain_private) decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
   int esc = 0;
   bool fail = false;
   for (int it = 0;; ++it) {
@@ -149,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     }
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
-    if (nxt < ntiles) load_fragments(slot((it + 1) % 3), stage(buf ^ 1), bars + (buf ^ 1));
+    if (nxt < ntiles) load_fragments<PUBIMG>(slot((it + 1) % 3), stage(buf ^ 1), bars + (buf ^ 1));
     const int k = K >= 0 ? K : sl->k;
     const int npub = 63 - k;
     const int nb = sl->nb;
@@ -215,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         }
       }
     }
-    if (nxt < ntiles) wait_fragments(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
+    if (nxt < ntiles) wait_fragments<PUBIMG>(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
     __syncthreads();                                                       // B
     {
       // queued pixels (from the last thread down) re-decided exactly while the first threads
@@ -234,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       }
       if (t == 0) misc[1] += misc[0];
     }
-    if (nxt < ntiles && !a.plain_private)
+    if (!PUBIMG && nxt < ntiles && !a.plain_private)
       decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
     fence_proxy_async();                                  // pixel writes before the bulk stores
     __syncthreads();                                                       // C
@@ -276,20 +293,25 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
   }
 }
 
-template <int K, bool BATCH>
+template <int K, bool BATCH, bool PUBIMG = false>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
-  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH>, kSmemBytes, attr);
+  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG>, kSmemBytes, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
   const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
-  if (grid > 0) restore_kernel<K, BATCH><<<grid, kThreads, kSmemBytes, s>>>(a);
+  if (grid > 0) restore_kernel<K, BATCH, PUBIMG><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
-// k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile
+// k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile;
+// a.public_image (one image) selects the public-image form
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
+  if (a.public_image) {
+    if (a.images || a.k < 0) return cudaErrorInvalidValue;
+    return a.k == 5 ? launch_k<5, false, true>(a, s, sms, per_sm) : launch_k<-1, false, true>(a, s, sms, per_sm);
+  }
   if (a.images) {
     if (a.k == 0) return launch_k<0, true>(a, s, sms, per_sm);
     if (a.k == 5) return launch_k<5, true>(a, s, sms, per_sm);

@@ -93,6 +93,8 @@ struct TileArgs {
   // protect of one image into packed streams: 11 or 8 bits per AC field (pub_out / priv_out
   // then point to the packed public stream and the packed private stream); 0 = int16
   int32_t pack;
+  // restore in the public-image form (one image): private positions zero, DC 1024
+  int32_t public_image;
 };
 
 // What a CTA knows about the tile it is working on (shared memory, filled one tile ahead).
@@ -116,6 +118,10 @@ cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_s
 // AES-128-CTR over a whole buffer (the full-encryption comparator)
 cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
                             const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms);
+// histogram and adjacent-pair sums of an H x W x 3 image (hist [3][256], sums [3][3][6],
+// both zero on entry)
+cudaError_t launch_image_stats(const uint8_t* img, int width, int height, unsigned long long* hist, long long* sums,
+                               cudaStream_t s, int sms);
 // bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
 cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
                           long long ncb, int k, int w, cudaStream_t s);
