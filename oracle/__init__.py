@@ -14,8 +14,12 @@ Plain, slow, obviously correct code, following the paper step by step:
             CTR mode of NIST SP 800-38A (Sect. 6.12: "AES with counter mode")
   fds.py    protect / restore: DCT -> int16 -> zigzag split -> AES-CTR on Part 1, and the
             inverse (Sect. 6.3.1, Fig. 6; Sect. 3.2 defragmentation)
+  pack.py   11-bit and 8-bit packed storage of the fragments (Sect. 6.4.3, Table 5)
+  public.py the public fragment as an image (Sect. 6.5.1, Fig. 10) and the histogram /
+            adjacent-pixel correlation statistics (Sect. 6.6)
+  strong.py strong level: public image XOR SHA-512 of Part 1 per block (Sect. 6.3.2, Fig. 8)
 
 Every function that is not pinned by a test against something other than itself says
 "parity unpinned" in its docstring.  None does at present.
 """
-from . import aes, dct, exact, fds  # noqa: F401
+from . import aes, dct, exact, fds, pack, public, strong  # noqa: F401
