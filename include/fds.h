@@ -281,6 +281,32 @@ int fds_public_image(const int16_t* public_in, int32_t width, int32_t height, in
 int fds_image_stats(const uint8_t* image, int32_t width, int32_t height, uint64_t* histogram_out,
                     int64_t* pair_sums_out, void* stream);
 
+/* Strong level of protection (Sect. 6.3.2, Fig. 8; Fig. 7 (d)).  The public fragment is the
+ * public image (as fds_public_image) with every channel-block's 64 pixels XORed with the
+ * SHA-512 digest (FIPS 180-4) of that block's Part 1 plaintext -- its k+1 int16 coefficients,
+ * little-endian, zigzag order -- digest byte 8y+x onto pixel (y, x) of the block, its channel.
+ * Part 1 is AES-128-CTR encrypted from the IV exactly as fds_protect_image's private output.
+ * Restore decrypts Part 1, removes the masks, recovers the public coefficients from the public
+ * image by the forward transform (exact rounding) and restores as fds_restore_image; the
+ * public image holds rounded, clamped bytes, so the result is close to, not equal to, the
+ * original (its PSNR is the measure, Sect. 6.4.3).
+ * fds_sizes_strong: public bytes (W x H x 3), private bytes (2 (k+1) per channel-block) and the
+ * scratch both calls need.  Pointers: device; images 8-byte aligned, private and scratch
+ * 16-byte aligned; scratch owned by the caller, overwritten.  Asynchronous on `stream`. */
+int fds_sizes_strong(int32_t width, int32_t height, int32_t k, uint64_t* public_bytes,
+                     uint64_t* private_bytes, uint64_t* scratch_bytes);
+int fds_protect_image_strong(const uint8_t* pixels, int32_t width, int32_t height, int32_t k,
+                             const uint8_t key[16], const uint8_t iv[16], uint8_t* public_image_out,
+                             uint8_t* private_out, void* scratch, void* stream);
+int fds_restore_image_strong(const uint8_t* public_image_in, const uint8_t* private_in,
+                             int32_t width, int32_t height, int32_t k, const uint8_t key[16],
+                             const uint8_t iv[16], uint8_t* pixels_out, void* scratch,
+                             void* stream);
+/* Diagnostics (host only): the SHA-512 constants the library computes from their definition
+ * (the first 64 fraction bits of the cube roots of the first 80 primes, of the square roots
+ * of the first 8).  k_out: host uint64 [80]; h0_out: host uint64 [8]. */
+int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]);
+
 /* Diagnostics (host only, no device needed): the tensor-core form's B operand as the kernel
  * holds it in shared memory -- row n = 64 l + 8u + v is limb l of the basis function
  * (u, v), K index 8y + x, 128-byte rows, 16-byte chunk c of row n stored at chunk c ^ (n & 7);

@@ -287,6 +287,60 @@ def correlation(sums) -> list:
     return out
 
 
+def sizes_strong(width: int, height: int, k: int) -> tuple[int, int, int]:
+    """fds_sizes_strong: (public image bytes, private bytes, scratch bytes)."""
+    pub, priv, scr = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.check(_lib.load().fds_sizes_strong(width, height, k, ctypes.byref(pub), ctypes.byref(priv),
+                                            ctypes.byref(scr)), "fds_sizes_strong")
+    return pub.value, priv.value, scr.value
+
+
+def protect_image_strong(pixels: torch.Tensor, key: bytes, iv: bytes, k: int,
+                         scratch: torch.Tensor | None = None, public: torch.Tensor | None = None,
+                         private: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """fds_protect_image_strong: (strong public image H x W x 3 uint8, Part 1 ciphertext)."""
+    w, h = _image_dims(pixels)
+    _, priv_b, scr_b = sizes_strong(w, h, k)
+    dev = pixels.device
+    if public is None:
+        public = torch.empty((h, w, 3), dtype=torch.uint8, device=dev)
+    if private is None:
+        private = torch.empty(priv_b, dtype=torch.uint8, device=dev)
+    if scratch is None:
+        scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
+    if public.shape != (h, w, 3) or public.dtype != torch.uint8 or private.numel() < priv_b:
+        raise ValueError("bad output buffers")
+    rc = _lib.load().fds_protect_image_strong(pixels.data_ptr(), w, h, k, _check_key(key, "key"),
+                                              _check_key(iv, "iv"), public.data_ptr(), private.data_ptr(),
+                                              scratch.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_protect_image_strong")
+    return public, private[:priv_b]
+
+
+def restore_image_strong(public: torch.Tensor, private: torch.Tensor, k: int, key: bytes, iv: bytes,
+                         scratch: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_restore_image_strong: the H x W x 3 uint8 image from the strong public image."""
+    w, h = _image_dims(public)
+    _, _, scr_b = sizes_strong(w, h, k)
+    dev = public.device
+    if scratch is None:
+        scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
+    if out is None:
+        out = torch.empty((h, w, 3), dtype=torch.uint8, device=dev)
+    rc = _lib.load().fds_restore_image_strong(public.data_ptr(), private.data_ptr(), w, h, k,
+                                              _check_key(key, "key"), _check_key(iv, "iv"), out.data_ptr(),
+                                              scratch.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_restore_image_strong")
+    return out
+
+
+def sha512_constants() -> tuple[list[int], list[int]]:
+    """fds_sha512_constants (host only): the 80 round constants and the 8 initial words."""
+    kk, hh = (ctypes.c_uint64 * 80)(), (ctypes.c_uint64 * 8)()
+    _lib.check(_lib.load().fds_sha512_constants(kk, hh), "fds_sha512_constants")
+    return list(kk), list(hh)
+
+
 def encrypt_full(data: torch.Tensor, key: bytes, iv: bytes,
                  out: torch.Tensor | None = None) -> torch.Tensor:
     """fds_encrypt_full: AES-128-CTR over the whole byte buffer (the full-encryption

@@ -263,6 +263,7 @@ int ensure_init(int* dev_out = nullptr) {
     if ((e = cudaGetSymbolAddress(&p, g_tcb1)) != cudaSuccess) return cuda_fail(e, "symbol address");
     tb.tc_b[1] = static_cast<const uint4*>(p);
   }
+  if ((e = upload_sha512_constants()) != cudaSuccess) return cuda_fail(e, "SHA-512 constants upload");
   for (int i = 0; i < FDS_MAX_KEYS; ++i)   // keys registered before this device was ready
     if (g_slots[i].used &&
         (e = cudaMemcpyToSymbol(g_rk, g_slots[i].rk, sizeof(g_slots[i].rk), 44 * 4 * i)) != cudaSuccess)
@@ -638,6 +639,110 @@ int fds_image_stats(const uint8_t* image, int32_t width, int32_t height, uint64_
   e = launch_image_stats(image, width, height, reinterpret_cast<unsigned long long*>(histogram_out),
                          reinterpret_cast<long long*>(pair_sums_out), s, g_tables[dev].sms);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "statistics launch");
+}
+
+// ---- strong level of protection (Sect. 6.3.2, Fig. 8)
+int fds_sizes_strong(int32_t width, int32_t height, int32_t k, uint64_t* public_bytes, uint64_t* private_bytes,
+                     uint64_t* scratch_bytes) {
+  uint64_t pub16 = 0, priv16 = 0;
+  int rc = fds_sizes(width, height, k, &pub16, &priv16);
+  if (rc) return rc;
+  const uint64_t px = (uint64_t)width * (uint64_t)height * 3ull;
+  if (public_bytes) *public_bytes = px;
+  if (private_bytes) *private_bytes = priv16;
+  // restore: Part 1 plaintext, the public image, its int16 public fragment, a private sink
+  if (scratch_bytes) *scratch_bytes = align16u(priv16) + align16u(px) + align16u(pub16) + align16u(priv16);
+  return FDS_OK;
+}
+
+static int strong_checks(int32_t width, int32_t height, int32_t k, const void* px, const void* img,
+                         const void* priv, const void* scratch, const void* key, const void* iv) {
+  if (bad_dims(width, height)) return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8");
+  if (k < 0 || k > 63) return set_err(FDS_E_INVALID, "k must be in 0..63");
+  if (!px || !img || !priv || !scratch || !key || !iv) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(px, 8) || misaligned(img, 8) || misaligned(priv, 16) || misaligned(scratch, 16))
+    return set_err(FDS_E_INVALID, "images must be 8-byte aligned, private and scratch 16-byte aligned");
+  return FDS_OK;
+}
+
+int fds_protect_image_strong(const uint8_t* pixels, int32_t width, int32_t height, int32_t k, const uint8_t key[16],
+                             const uint8_t iv[16], uint8_t* public_image_out, uint8_t* private_out, void* scratch,
+                             void* stream) {
+  int rc = strong_checks(width, height, k, pixels, public_image_out, private_out, scratch, key, iv);
+  if (rc) return rc;
+  uint64_t pub16 = 0, priv16 = 0;
+  fds_sizes(width, height, k, &pub16, &priv16);
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int16_t* s_pub = static_cast<int16_t*>(scratch);
+  uint8_t* s_plain = static_cast<uint8_t*>(scratch) + align16u(pub16);
+  TileArgs a{};                                  // 1. transform, Part 1 left in plaintext
+  a.pixels_in = pixels;
+  a.pub_out = s_pub;
+  a.priv_out = s_plain;
+  a.plain_private = 1;
+  fill_geometry(a, width, height, k);
+  expand_key(key, a.rk);
+  iv_words(iv, &a.iv_hi, &a.iv_lo);
+  if ((rc = run_protect(a, dev, s, false))) return rc;
+  TileArgs b{};                                  // 2. the public image
+  b.pub_in = s_pub;
+  b.pixels_out = public_image_out;
+  b.public_image = 1;
+  fill_geometry(b, width, height, k);
+  if ((rc = run_restore(b, dev, s))) return rc;
+  cudaError_t e = launch_strong_mask(s_plain, public_image_out, public_image_out, width, height, k, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mask launch");   // 3. XOR the SHA-512 masks
+  e = launch_aes_full(s_plain, private_out, priv16, a.iv_hi, a.iv_lo, a.rk, g_tables[dev].T, s,
+                      g_tables[dev].sms);        // 4. encrypt Part 1
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "encryption launch");
+}
+
+int fds_restore_image_strong(const uint8_t* public_image_in, const uint8_t* private_in, int32_t width,
+                             int32_t height, int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                             uint8_t* pixels_out, void* scratch, void* stream) {
+  int rc = strong_checks(width, height, k, pixels_out, public_image_in, private_in, scratch, key, iv);
+  if (rc) return rc;
+  uint64_t pub16 = 0, priv16 = 0;
+  fds_sizes(width, height, k, &pub16, &priv16);
+  const uint64_t px = (uint64_t)width * (uint64_t)height * 3ull;
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t* s_plain = static_cast<uint8_t*>(scratch);
+  uint8_t* s_img = s_plain + align16u(priv16);
+  int16_t* s_pub = reinterpret_cast<int16_t*>(s_img + align16u(px));
+  uint8_t* s_sink = reinterpret_cast<uint8_t*>(s_pub) + align16u(pub16);
+  uint32_t rk[44];
+  expand_key(key, rk);
+  uint64_t hi, lo;
+  iv_words(iv, &hi, &lo);
+  cudaError_t e = launch_aes_full(private_in, s_plain, priv16, hi, lo, rk, g_tables[dev].T, s,
+                                  g_tables[dev].sms);   // 1. decrypt Part 1
+  if (e != cudaSuccess) return cuda_fail(e, "decryption launch");
+  e = launch_strong_mask(s_plain, public_image_in, s_img, width, height, k, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mask launch");   // 2. remove the masks
+  TileArgs a{};                                  // 3. the public coefficients of the public image
+  a.pixels_in = s_img;
+  a.pub_out = s_pub;
+  a.priv_out = s_sink;
+  a.plain_private = 1;
+  fill_geometry(a, width, height, k);
+  if ((rc = run_protect(a, dev, s, false))) return rc;
+  TileArgs b{};                                  // 4. restore from plaintext Part 1
+  b.pub_in = s_pub;
+  b.priv_in = s_plain;
+  b.pixels_out = pixels_out;
+  b.plain_private = 1;
+  fill_geometry(b, width, height, k);
+  return run_restore(b, dev, s);
+}
+
+int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]) {
+  if (!k_out || !h0_out) return set_err(FDS_E_INVALID, "null pointer argument");
+  sha512_constants(k_out, h0_out);
+  return FDS_OK;
 }
 
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {

@@ -122,6 +122,12 @@ cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uin
 // both zero on entry)
 cudaError_t launch_image_stats(const uint8_t* img, int width, int height, unsigned long long* hist, long long* sums,
                                cudaStream_t s, int sms);
+// strong level: out = in XOR (per channel-block SHA-512 of its Part 1 plaintext, [ncb][k+1]
+// int16); the constants are uploaded once per device by upload_sha512_constants
+cudaError_t launch_strong_mask(const uint8_t* plain, const uint8_t* in, uint8_t* out, int width, int height, int k,
+                               cudaStream_t s);
+cudaError_t upload_sha512_constants();
+void sha512_constants(uint64_t k[80], uint64_t h0[8]);
 // bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
 cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
                           long long ncb, int k, int w, cudaStream_t s);

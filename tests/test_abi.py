@@ -139,3 +139,56 @@ def test_packed_storage_sizes_and_checks(lib):
     key = bytes(16)
     assert lib.fds_protect_image_packed(11, 8, 64, 64, 0, key, key, 1, 24, 32, None) == -1   # private not 16-aligned
     assert lib.fds_protect_image_packed(11, 8, 64, 64, 0, key, key, 1, 32, None, None) == -1  # no scratch
+
+
+def _primes(n):
+    out, p = [], 2
+    while len(out) < n:
+        if all(p % q for q in out if q * q <= p):
+            out.append(p)
+        p += 1
+    return out
+
+
+def _icbrt(n):
+    """floor(n^(1/3)) for a non-negative integer, by Newton's method on integers."""
+    x = 1 << ((n.bit_length() + 2) // 3 + 1)
+    while True:
+        y = (2 * x + n // (x * x)) // 3
+        if y >= x:
+            break
+        x = y
+    while x ** 3 > n:
+        x -= 1
+    while (x + 1) ** 3 <= n:
+        x += 1
+    return x
+
+
+def test_sha512_constants_follow_their_definition(lib):
+    # FIPS 180-4: the first 64 bits of the fractional parts of the cube roots of the first 80
+    # primes and of the square roots of the first 8
+    import math
+
+    from paper_1512_02951_gb300 import api
+
+    kk, hh = api.sha512_constants()
+    mask = (1 << 64) - 1
+    ps = _primes(80)
+    assert kk == [_icbrt(p << 192) & mask for p in ps]
+    assert hh == [math.isqrt(p << 128) & mask for p in ps[:8]]
+
+
+def test_strong_level_sizes_and_checks(lib):
+    from paper_1512_02951_gb300 import api
+
+    pub, priv, scr = api.sizes_strong(64, 48, 5)
+    assert pub == 64 * 48 * 3 and priv == ofds.sizes(64, 48, 5)[1]
+    assert scr >= priv + pub + ofds.sizes(64, 48, 5)[0] + priv
+    u = ctypes.c_uint64()
+    assert lib.fds_sizes_strong(60, 48, 5, ctypes.byref(u), ctypes.byref(u), ctypes.byref(u)) != 0
+    key = bytes(16)
+    # null / misaligned pointers fail on the host, before any device work
+    assert lib.fds_protect_image_strong(None, 64, 48, 5, key, key, 16, 16, 16, None) != 0
+    assert lib.fds_protect_image_strong(16, 64, 48, 5, key, key, 16, 24, 16, None) != 0
+    assert lib.fds_restore_image_strong(16, 16, 64, 48, 64, key, key, 16, 16, None) != 0
