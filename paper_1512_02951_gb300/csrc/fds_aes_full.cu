@@ -8,6 +8,7 @@
 // filled once by the persistent CTAs).  The round keys sit in the kernel's parameter space.
 // A trailing partial block is handled byte by byte.
 #include "fds_tile.cuh"
+#include "fds_aux.h"
 
 namespace fds {
 

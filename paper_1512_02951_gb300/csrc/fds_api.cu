@@ -12,6 +12,7 @@
 
 #include "fds.h"
 #include "fds_tile.cuh"
+#include "fds_aux.h"
 
 namespace fds {
 

@@ -1,0 +1,26 @@
+// Launchers of the kernels outside the tile machinery (one translation unit each): the
+// full-encryption comparator, packed-storage unpacking, image statistics and the strong
+// level's SHA-512 masks.  Host code only needs <cuda_runtime.h>.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fds {
+
+// AES-128-CTR over a whole buffer (the full-encryption comparator)
+cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
+                            const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms);
+// histogram and adjacent-pair sums of an H x W x 3 image (hist [3][256], sums [3][3][6],
+// both zero on entry)
+cudaError_t launch_image_stats(const uint8_t* img, int width, int height, unsigned long long* hist, long long* sums,
+                               cudaStream_t s, int sms);
+// strong level: out = in XOR (per channel-block SHA-512 of its Part 1 plaintext, [ncb][k+1]
+// int16); the constants are uploaded once per device by upload_sha512_constants
+cudaError_t launch_strong_mask(const uint8_t* plain, const uint8_t* in, uint8_t* out, int width, int height, int k,
+                               cudaStream_t s);
+cudaError_t upload_sha512_constants();
+void sha512_constants(uint64_t k[80], uint64_t h0[8]);
+// bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
+cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
+                          long long ncb, int k, int w, cudaStream_t s);
+}  // namespace fds

@@ -17,6 +17,7 @@
 // One launch does both streams: the first blocks of the grid take the public stream, the
 // rest the private one.
 #include "fds_tile.cuh"
+#include "fds_aux.h"
 
 namespace fds {
 

@@ -7,6 +7,7 @@
 // the same channel of the interleaved row.  Per-thread 64-bit accumulators and a shared
 // histogram, reduced per CTA in shared memory and added to the device outputs with atomics.
 #include "fds_tile.cuh"
+#include "fds_aux.h"
 
 namespace fds {
 

@@ -9,6 +9,7 @@
 // roots and uploaded once per device.  One thread per channel-block; the message of a
 // channel-block (2 (k + 1) bytes) takes one 1024-bit block up to k = 54, two beyond.
 #include "fds_tile.cuh"
+#include "fds_aux.h"
 
 namespace fds {
 

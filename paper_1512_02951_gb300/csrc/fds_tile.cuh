@@ -115,22 +115,6 @@ struct TileSlot {
 // resident CTAs per SM to launch (1 or 2)
 cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 2);
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 2);
-// AES-128-CTR over a whole buffer (the full-encryption comparator)
-cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
-                            const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms);
-// histogram and adjacent-pair sums of an H x W x 3 image (hist [3][256], sums [3][3][6],
-// both zero on entry)
-cudaError_t launch_image_stats(const uint8_t* img, int width, int height, unsigned long long* hist, long long* sums,
-                               cudaStream_t s, int sms);
-// strong level: out = in XOR (per channel-block SHA-512 of its Part 1 plaintext, [ncb][k+1]
-// int16); the constants are uploaded once per device by upload_sha512_constants
-cudaError_t launch_strong_mask(const uint8_t* plain, const uint8_t* in, uint8_t* out, int width, int height, int k,
-                               cudaStream_t s);
-cudaError_t upload_sha512_constants();
-void sha512_constants(uint64_t k[80], uint64_t h0[8]);
-// bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
-cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
-                          long long ncb, int k, int w, cudaStream_t s);
 // tensor-core protect of one image (form 0: BF16 three limbs, 1: TF32 two limbs); tiles of
 // 128 channel-blocks, two CTAs per SM
 cudaError_t launch_protect_tc(const TileArgs& a, cudaStream_t s, int form, bool debug, int sms);
