@@ -20,31 +20,36 @@ constexpr int kMaskThreads = 128;
 
 __device__ __forceinline__ uint64_t rotr64(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
 
-// one SHA-512 compression of the 16 big-endian words w into state h
+// one SHA-512 compression of the 16 big-endian words w into state h; the 80 rounds run as
+// five passes of 16 (the schedule ring index is then fixed in each unrolled round, and the
+// code stays small enough for the instruction cache)
 __device__ __forceinline__ void sha512_compress(uint64_t (&h)[8], uint64_t (&w)[16]) {
   uint64_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
+#pragma unroll 1
+  for (int t0 = 0; t0 < 80; t0 += 16) {
 #pragma unroll
-  for (int t = 0; t < 80; ++t) {
-    if (t >= 16) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
-      const uint64_t x15 = w[(t + 1) & 15], x2 = w[(t + 14) & 15];
-      const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
-      const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
-      w[t & 15] += s0 + w[(t + 9) & 15] + s1;
+    for (int j = 0; j < 16; ++j) {
+      if (t0 > 0) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
+        const uint64_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
+        const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
+        const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
+        w[j] += s0 + w[(j + 9) & 15] + s1;
+      }
+      const uint64_t S1 = rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41);
+      const uint64_t ch = (e & f) ^ (~e & g);
+      const uint64_t t1 = hh + S1 + ch + c_sha_k[t0 + j] + w[j];
+      const uint64_t S0 = rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39);
+      const uint64_t maj = (a & b) ^ (a & c) ^ (b & c);
+      const uint64_t t2 = S0 + maj;
+      hh = g;
+      g = f;
+      f = e;
+      e = d + t1;
+      d = c;
+      c = b;
+      b = a;
+      a = t1 + t2;
     }
-    const uint64_t S1 = rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41);
-    const uint64_t ch = (e & f) ^ (~e & g);
-    const uint64_t t1 = hh + S1 + ch + c_sha_k[t] + w[t & 15];
-    const uint64_t S0 = rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39);
-    const uint64_t maj = (a & b) ^ (a & c) ^ (b & c);
-    const uint64_t t2 = S0 + maj;
-    hh = g;
-    g = f;
-    f = e;
-    e = d + t1;
-    d = c;
-    c = b;
-    b = a;
-    a = t1 + t2;
   }
   h[0] += a;
   h[1] += b;
