@@ -778,6 +778,13 @@ def strong_arm(args):
     r_ms = timed(lambda: api.restore_image_strong(pub, priv, K_SEL, key, iv, scratch, out))
     full_ms = timed(lambda: api.encrypt_full(img, key, iv, out=full_out))
     back = out.cpu().numpy()
+    pub16, _ = api.protect_image(img, key, iv, K_SEL)
+    pimg = torch.empty_like(img)
+    pi_ms = timed(lambda: api.public_image(pub16, WIDTH, HEIGHT, K_SEL, pimg))
+    st_ms = timed(lambda: api.image_stats(img))
+    r_img = api.correlation(api.image_stats(img)[1])
+    r_pub = api.correlation(api.image_stats(pimg)[1])
+    r_strong = api.correlation(api.image_stats(pub)[1])
     mse = float(np.mean((back.astype(np.float64) - img_np.astype(np.float64)) ** 2))
     res = {"protect_ms": round(p_ms, 5), "restore_ms": round(r_ms, 5),
            "protect_MBps": round(px_bytes / (p_ms * 1e-3) / 1e6, 1),
@@ -785,7 +792,15 @@ def strong_arm(args):
            "full_aes128_ctr_ms": round(full_ms, 5),
            "protect_time_vs_full_encryption": round(p_ms / full_ms, 3),
            "restore_psnr_db": round(10.0 * np.log10(255.0 ** 2 / mse), 3) if mse else None,
-           "restore_exact_fraction": round(float((back == img_np).mean()), 5)}
+           "restore_exact_fraction": round(float((back == img_np).mean()), 5),
+           "public_image_ms": round(pi_ms, 5),
+           "public_image_GBps": round((2 * (63 - K_SEL) / 64 + 1) * px_bytes / (pi_ms * 1e-3) / 1e9, 1),
+           "image_stats_ms": round(st_ms, 5),
+           "adjacent_pixel_correlation": {
+               "original": [[round(v, 4) for v in row] for row in r_img],
+               "public_image": [[round(v, 4) for v in row] for row in r_pub],
+               "strong_public_image": [[round(v, 4) for v in row] for row in r_strong],
+               "order": "[right, down, down-right][R, G, B]"}}
     line = {"metric": "strong-level protect throughput, MB/s of pixels",
             "value": res["protect_MBps"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["protect_ms"],
@@ -795,7 +810,7 @@ def strong_arm(args):
                                    "XOR SHA-512 of Part 1) vs AES-128-CTR of all pixel bytes",
                        "l2": "256 MB buffer written between timed launches"},
             "results": res,
-            "gpu_launches": args.steps * (4 + 4 + 1)}
+            "gpu_launches": args.steps * (4 + 4 + 1 + 1 + 1)}
     print(json.dumps(line), flush=True)
 
 
