@@ -18,8 +18,10 @@ Plain, slow, obviously correct code, following the paper step by step:
   public.py the public fragment as an image (Sect. 6.5.1, Fig. 10) and the histogram /
             adjacent-pixel correlation statistics (Sect. 6.6)
   strong.py strong level: public image XOR SHA-512 of Part 1 per block (Sect. 6.3.2, Fig. 8)
+  dwt.py    the lossless DWT scheme: Le Gall 5/3 lifting, AES-CTR on level 1, SHA-256 /
+            SHA-512 masks on levels 2 and 3 (Sect. 6.8-6.12, Fig. 18)
 
 Every function that is not pinned by a test against something other than itself says
 "parity unpinned" in its docstring.  None does at present.
 """
-from . import aes, dct, exact, fds, pack, public, strong  # noqa: F401
+from . import aes, dct, dwt, exact, fds, pack, public, strong  # noqa: F401
