@@ -302,6 +302,33 @@ int fds_restore_image_strong(const uint8_t* public_image_in, const uint8_t* priv
                              int32_t width, int32_t height, int32_t k, const uint8_t key[16],
                              const uint8_t iv[16], uint8_t* pixels_out, void* scratch,
                              void* stream);
+/* Selective encryption with the DWT (Sect. 6.8-6.12, Figs. 16-18): lossless, for any data.
+ * The data is an H x W matrix of bytes (W, H multiples of 8; arbitrary bytes fill W-byte rows,
+ * zero-padded to whole 8-row blocks, Sect. 6.9.3).  Per 8x8 block, in raster order: the bytes
+ * minus 128 go through a two-level reversible Le Gall 5/3 DWT (integer lifting, the invertible
+ * JPEG 2000 form of Eqs. 1-2: d[n] = x[2n+1] - floor((x[2n] + x[2n+2]) / 2), s[n] = x[2n] +
+ * floor((d[n-1] + d[n] + 2) / 4), whole-sample symmetric extension; rows, then columns);
+ *   level 1 = second-level LL (4 x 10-bit fields = 5 bytes), AES-128-CTR encrypted as one
+ *             message from the IV over all blocks' level-1 bytes;
+ *   level 2 = second-level HL, LH (10 bits) and HH (11 bits): 124 bits in 16 bytes, XORed
+ *             with bytes 0..15 of SHA-256(key || IV || block index as 8 bytes big-endian ||
+ *             level 1 plaintext);
+ *   level 3 = first-level HL, LH, HH, 48 x 10 bits = 60 bytes, XORed with bytes 0..59 of
+ *             SHA-512(key || IV || block index || level 2 plaintext).
+ * Fields are two's complement, least significant bit first; quadrants in the order HL, LH,
+ * HH, each row-major.  Levels 1 and 2 are the private fragment, level 3 the public one.
+ * Restore inverts every step exactly.
+ * Pointers: device; data 8-byte aligned, level streams 16-byte aligned (5, 16 and 60 bytes per
+ * block: fds_dwt_sizes).  Asynchronous on `stream`; argument errors are returned at once. */
+int fds_dwt_sizes(int32_t width, int32_t height, uint64_t* level1_bytes, uint64_t* level2_bytes,
+                  uint64_t* level3_bytes);
+int fds_dwt_protect(const uint8_t* data, int32_t width, int32_t height, const uint8_t key[16],
+                    const uint8_t iv[16], uint8_t* level1_out, uint8_t* level2_out,
+                    uint8_t* level3_out, void* stream);
+int fds_dwt_restore(const uint8_t* level1_in, const uint8_t* level2_in, const uint8_t* level3_in,
+                    int32_t width, int32_t height, const uint8_t key[16], const uint8_t iv[16],
+                    uint8_t* data_out, void* stream);
+
 /* Diagnostics (host only): the SHA-512 constants the library computes from their definition
  * (the first 64 fraction bits of the cube roots of the first 80 primes, of the square roots
  * of the first 8).  k_out: host uint64 [80]; h0_out: host uint64 [8]. */

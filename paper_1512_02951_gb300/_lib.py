@@ -110,6 +110,14 @@ SIGNATURES = {
                                                 ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
     "fds_sha512_constants": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "fds_dwt_sizes": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "fds_dwt_protect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                                       ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "fds_dwt_restore": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "fds_tc_basis": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64,
                                     ctypes.POINTER(ctypes.c_double)]),
     "fds_debug_dct_tc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,

@@ -334,6 +334,55 @@ def restore_image_strong(public: torch.Tensor, private: torch.Tensor, k: int, ke
     return out
 
 
+def dwt_sizes(width: int, height: int) -> tuple[int, int, int]:
+    """fds_dwt_sizes: bytes of level 1, level 2 and level 3 (5, 16, 60 per 8x8 block)."""
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.check(_lib.load().fds_dwt_sizes(width, height, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "fds_dwt_sizes")
+    return a.value, b.value, c.value
+
+
+def bytes_to_matrix(data: torch.Tensor, width: int) -> torch.Tensor:
+    """Agnostic chunking (Sect. 6.9.3): a 1-D uint8 tensor as rows of `width` bytes, zero-padded
+    to whole 8-row blocks (the caller keeps the original length)."""
+    if width <= 0 or width % 8:
+        raise ValueError("width must be a positive multiple of 8")
+    n = data.numel()
+    rows = -(-n // width)                   # ceil(n / width)
+    rows = max(8, -(-rows // 8) * 8)        # whole 8-row blocks
+    out = torch.zeros(rows * width, dtype=torch.uint8, device=data.device)
+    out[:n] = data.reshape(-1)
+    return out.reshape(rows, width)
+
+
+def dwt_protect(data: torch.Tensor, key: bytes, iv: bytes, out: tuple | None = None):
+    """fds_dwt_protect: (level 1 ciphertext, level 2 masked, level 3 masked) uint8 device
+    tensors of an H x W uint8 matrix."""
+    if data.dtype != torch.uint8 or data.dim() != 2 or not data.is_contiguous() or not data.is_cuda:
+        raise ValueError("data must be a contiguous H x W uint8 CUDA tensor")
+    h, w = data.shape
+    sizes = dwt_sizes(w, h)
+    if out is None:
+        out = tuple(torch.empty(n, dtype=torch.uint8, device=data.device) for n in sizes)
+    rc = _lib.load().fds_dwt_protect(data.data_ptr(), w, h, _check_key(key, "key"), _check_key(iv, "iv"),
+                                     out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(),
+                                     _stream_ptr(data.device))
+    _lib.check(rc, "fds_dwt_protect")
+    return out
+
+
+def dwt_restore(level1: torch.Tensor, level2: torch.Tensor, level3: torch.Tensor, width: int, height: int,
+                key: bytes, iv: bytes, out: torch.Tensor | None = None) -> torch.Tensor:
+    """fds_dwt_restore: the H x W uint8 matrix back, exactly."""
+    dev = level1.device
+    if out is None:
+        out = torch.empty((height, width), dtype=torch.uint8, device=dev)
+    rc = _lib.load().fds_dwt_restore(level1.data_ptr(), level2.data_ptr(), level3.data_ptr(), width, height,
+                                     _check_key(key, "key"), _check_key(iv, "iv"), out.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_dwt_restore")
+    return out
+
+
 def sha512_constants() -> tuple[list[int], list[int]]:
     """fds_sha512_constants (host only): the 80 round constants and the 8 initial words."""
     kk, hh = (ctypes.c_uint64 * 80)(), (ctypes.c_uint64 * 8)()

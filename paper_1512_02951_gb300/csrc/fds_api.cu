@@ -265,6 +265,7 @@ int ensure_init(int* dev_out = nullptr) {
     tb.tc_b[1] = static_cast<const uint4*>(p);
   }
   if ((e = upload_sha512_constants()) != cudaSuccess) return cuda_fail(e, "SHA-512 constants upload");
+  if ((e = upload_dwt_constants()) != cudaSuccess) return cuda_fail(e, "SHA constants upload");
   for (int i = 0; i < FDS_MAX_KEYS; ++i)   // keys registered before this device was ready
     if (g_slots[i].used &&
         (e = cudaMemcpyToSymbol(g_rk, g_slots[i].rk, sizeof(g_slots[i].rk), 44 * 4 * i)) != cudaSuccess)
@@ -738,6 +739,52 @@ int fds_restore_image_strong(const uint8_t* public_image_in, const uint8_t* priv
   b.plain_private = 1;
   fill_geometry(b, width, height, k);
   return run_restore(b, dev, s);
+}
+
+// ---- the DWT scheme (Sect. 6.8-6.12, Fig. 18)
+int fds_dwt_sizes(int32_t width, int32_t height, uint64_t* level1_bytes, uint64_t* level2_bytes,
+                  uint64_t* level3_bytes) {
+  if (bad_dims(width, height)) return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8");
+  const uint64_t nb = (uint64_t)(width / 8) * (uint64_t)(height / 8);
+  if (level1_bytes) *level1_bytes = 5 * nb;
+  if (level2_bytes) *level2_bytes = 16 * nb;
+  if (level3_bytes) *level3_bytes = 60 * nb;
+  return FDS_OK;
+}
+
+static int dwt_checks(int32_t width, int32_t height, const void* data, const void* l1, const void* l2,
+                      const void* l3, const void* key, const void* iv) {
+  if (bad_dims(width, height)) return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8");
+  if (!data || !l1 || !l2 || !l3 || !key || !iv) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(data, 8) || misaligned(l1, 16) || misaligned(l2, 16) || misaligned(l3, 16))
+    return set_err(FDS_E_INVALID, "data must be 8-byte aligned, the level streams 16-byte aligned");
+  return FDS_OK;
+}
+
+int fds_dwt_protect(const uint8_t* data, int32_t width, int32_t height, const uint8_t key[16], const uint8_t iv[16],
+                    uint8_t* level1_out, uint8_t* level2_out, uint8_t* level3_out, void* stream) {
+  int rc = dwt_checks(width, height, data, level1_out, level2_out, level3_out, key, iv);
+  if (rc) return rc;
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  uint32_t rk[44];
+  expand_key(key, rk);
+  const cudaError_t e = launch_dwt_protect(data, width, height, key, iv, rk, g_tables[dev].T, level1_out,
+                                           level2_out, level3_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "DWT protect launch");
+}
+
+int fds_dwt_restore(const uint8_t* level1_in, const uint8_t* level2_in, const uint8_t* level3_in, int32_t width,
+                    int32_t height, const uint8_t key[16], const uint8_t iv[16], uint8_t* data_out, void* stream) {
+  int rc = dwt_checks(width, height, data_out, level1_in, level2_in, level3_in, key, iv);
+  if (rc) return rc;
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  uint32_t rk[44];
+  expand_key(key, rk);
+  const cudaError_t e = launch_dwt_restore(level1_in, level2_in, level3_in, width, height, key, iv, rk,
+                                           g_tables[dev].T, data_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "DWT restore launch");
 }
 
 int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]) {

@@ -20,6 +20,16 @@ cudaError_t launch_strong_mask(const uint8_t* plain, const uint8_t* in, uint8_t*
                                cudaStream_t s);
 cudaError_t upload_sha512_constants();
 void sha512_constants(uint64_t k[80], uint64_t h0[8]);
+// the DWT scheme: per 8x8 block of an H x W byte matrix, level 1 (5 bytes, AES-CTR), level 2
+// (16 bytes, SHA-256 masked), level 3 (60 bytes, SHA-512 masked); constants uploaded once per
+// device by upload_dwt_constants
+cudaError_t launch_dwt_protect(const uint8_t* data, int width, int height, const uint8_t key[16],
+                               const uint8_t iv[16], const uint32_t rk[44], const uint32_t* T, uint8_t* l1,
+                               uint8_t* l2, uint8_t* l3, cudaStream_t s);
+cudaError_t launch_dwt_restore(const uint8_t* l1, const uint8_t* l2, const uint8_t* l3, int width, int height,
+                               const uint8_t key[16], const uint8_t iv[16], const uint32_t rk[44],
+                               const uint32_t* T, uint8_t* data, cudaStream_t s);
+cudaError_t upload_dwt_constants();
 // bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
 cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
                           long long ncb, int k, int w, cudaStream_t s);

@@ -3,63 +3,18 @@
 // k + 1 int16 little-endian, plaintext), digest byte 8 y + x onto pixel (y, x) of the block --
 // 512 bits for 64 pixels.  The XOR is its own inverse, so the same kernel masks and unmasks.
 //
-// SHA-512 is written from FIPS 180-4: 64-bit words, 80 rounds, a 16-word message schedule
-// ring.  Its constants (the first 64 fraction bits of the cube roots of the first 80 primes
-// and of the square roots of the first 8) are computed here on the host with exact integer
-// roots and uploaded once per device.  One thread per channel-block; the message of a
-// channel-block (2 (k + 1) bytes) takes one 1024-bit block up to k = 54, two beyond.
+// SHA-512 (fds_sha.cuh) is written from FIPS 180-4; its constants (the first 64 fraction bits
+// of the cube roots of the first 80 primes and of the square roots of the first 8) are
+// computed here on the host with exact integer roots and uploaded once per device.  One
+// thread per channel-block; the message of a channel-block (2 (k + 1) bytes) takes one
+// 1024-bit block up to k = 54, two beyond.
 #include "fds_tile.cuh"
 #include "fds_aux.h"
+#include "fds_sha.cuh"
 
 namespace fds {
 
-__constant__ uint64_t c_sha_k[80];
-__constant__ uint64_t c_sha_h0[8];
-
 constexpr int kMaskThreads = 128;
-
-__device__ __forceinline__ uint64_t rotr64(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
-
-// one SHA-512 compression of the 16 big-endian words w into state h; the 80 rounds run as
-// five passes of 16 (the schedule ring index is then fixed in each unrolled round, and the
-// code stays small enough for the instruction cache)
-__device__ __forceinline__ void sha512_compress(uint64_t (&h)[8], uint64_t (&w)[16]) {
-  uint64_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
-#pragma unroll 1
-  for (int t0 = 0; t0 < 80; t0 += 16) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (t0 > 0) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
-        const uint64_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
-        const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
-        const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
-        w[j] += s0 + w[(j + 9) & 15] + s1;
-      }
-      const uint64_t S1 = rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41);
-      const uint64_t ch = (e & f) ^ (~e & g);
-      const uint64_t t1 = hh + S1 + ch + c_sha_k[t0 + j] + w[j];
-      const uint64_t S0 = rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39);
-      const uint64_t maj = (a & b) ^ (a & c) ^ (b & c);
-      const uint64_t t2 = S0 + maj;
-      hh = g;
-      g = f;
-      f = e;
-      e = d + t1;
-      d = c;
-      c = b;
-      b = a;
-      a = t1 + t2;
-    }
-  }
-  h[0] += a;
-  h[1] += b;
-  h[2] += c;
-  h[3] += d;
-  h[4] += e;
-  h[5] += f;
-  h[6] += g;
-  h[7] += hh;
-}
 
 // padded message byte m of the L-byte message msg (one or two 128-byte blocks)
 __device__ __forceinline__ uint32_t msg_byte(const uint8_t* msg, int L, int m, int nblk) {
@@ -79,7 +34,7 @@ __device__ __forceinline__ void sha512_part1(const uint8_t* msg, int k, uint64_t
   const int L = 2 * ((K >= 0 ? K : k) + 1);
   const int nblk = L + 17 <= 128 ? 1 : 2;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) h[i] = c_sha_h0[i];
+  for (int i = 0; i < 8; ++i) h[i] = c_sha512_h0[i];
   for (int blk = 0; blk < nblk; ++blk) {
     uint64_t w[16];
 #pragma unroll
@@ -218,12 +173,6 @@ void sha512_constants(uint64_t k[80], uint64_t h0[8]) {
   }
 }
 
-cudaError_t upload_sha512_constants() {
-  uint64_t kk[80], h0[8];
-  sha512_constants(kk, h0);
-  cudaError_t e = cudaMemcpyToSymbol(c_sha_k, kk, sizeof(kk));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sha_h0, h0, sizeof(h0));
-  return e;
-}
+cudaError_t upload_sha512_constants() { return upload_sha_tables(); }
 
 }  // namespace fds

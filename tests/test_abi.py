@@ -192,3 +192,15 @@ def test_strong_level_sizes_and_checks(lib):
     assert lib.fds_protect_image_strong(None, 64, 48, 5, key, key, 16, 16, 16, None) != 0
     assert lib.fds_protect_image_strong(16, 64, 48, 5, key, key, 16, 24, 16, None) != 0
     assert lib.fds_restore_image_strong(16, 16, 64, 48, 64, key, key, 16, 16, None) != 0
+
+
+def test_dwt_sizes_and_checks(lib):
+    from paper_1512_02951_gb300 import api
+
+    assert api.dwt_sizes(64, 48) == (5 * 48, 16 * 48, 60 * 48)
+    u = ctypes.c_uint64()
+    assert lib.fds_dwt_sizes(60, 48, ctypes.byref(u), ctypes.byref(u), ctypes.byref(u)) != 0
+    key = bytes(16)
+    assert lib.fds_dwt_protect(None, 64, 48, key, key, 16, 16, 16, None) != 0
+    assert lib.fds_dwt_protect(16, 64, 48, key, key, 16, 24, 16, None) != 0     # misaligned level 2
+    assert lib.fds_dwt_restore(16, 16, 16, 64, 44, key, key, 16, None) != 0      # H not a multiple of 8
