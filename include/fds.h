@@ -258,6 +258,30 @@ int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8
                              const uint8_t iv[16], uint8_t* pixels_out, void* scratch,
                              void* stream);
 
+/* Protect / restore with host buffers, the copies overlapped with the kernels (the paper
+ * overlaps host and GPU work across images, Sect. 6.5, Fig. 11, Fig. 26; here within one image).
+ * The image is cut into `strips` runs of block rows (multiples of 8 rows, so each run's private
+ * bytes start on a keystream block); per strip, host -> device copy, kernel and device -> host
+ * copy run on three streams joined by events, so copies in both directions overlap the
+ * kernels of other strips.  Results are byte-identical to fds_protect_image /
+ * fds_restore_image.  fds_protect_image_host: host_pixels (pinned host, H x W x 3) is copied
+ * to dev_pixels, protected into dev_public / dev_private (device, kept for later use) and
+ * both fragments are copied to host_public / host_private (pinned host).
+ * fds_restore_image_host: restores dev_public / dev_private into dev_pixels and copies the
+ * pixels to host_pixels.  Kernels run on `stream`: earlier work on it comes
+ * first (the copy streams wait for it), and when it completes every copy of the call has
+ * completed.  strips: 1..64.
+ * Device alignments as fds_protect_image; host buffers should be pinned (pageable memory
+ * works but does not overlap). */
+int fds_protect_image_host(const uint8_t* host_pixels, uint8_t* dev_pixels, int32_t width,
+                           int32_t height, int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                           int16_t* dev_public, uint8_t* dev_private, int16_t* host_public,
+                           uint8_t* host_private, int32_t strips, void* stream);
+int fds_restore_image_host(const int16_t* dev_public, const uint8_t* dev_private,
+                           uint8_t* dev_pixels, uint8_t* host_pixels, int32_t width, int32_t height,
+                           int32_t k, const uint8_t key[16], const uint8_t iv[16], int32_t strips,
+                           void* stream);
+
 /* The paper's own form of the public fragment (Sect. 6.5.1, Fig. 10; Fig. 7 (b)): the public
  * coefficients as an image.  Per channel-block the zigzag positions 1..k are zero and the DC
  * coefficient is 1024 (= 8 x 128: the zero-mean block shifted to mid-grey), the positions

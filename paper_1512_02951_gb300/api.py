@@ -241,6 +241,40 @@ def restore_image_packed(public: torch.Tensor, private: torch.Tensor, width: int
     return out
 
 
+def protect_image_host(host_pixels: torch.Tensor, dev_pixels: torch.Tensor, key: bytes, iv: bytes, k: int,
+                       dev_public: torch.Tensor, dev_private: torch.Tensor, host_public: torch.Tensor,
+                       host_private: torch.Tensor, strips: int = 8) -> None:
+    """fds_protect_image_host: host pixels -> device -> protect -> both fragments back to the
+    host, by strips with the copies overlapped (host tensors should be pinned)."""
+    w, h = int(host_pixels.shape[1]), int(host_pixels.shape[0])
+    for t in (host_pixels, host_public, host_private):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+    for t in (dev_pixels, dev_public, dev_private):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("device buffers must be contiguous CUDA tensors")
+    rc = _lib.load().fds_protect_image_host(host_pixels.data_ptr(), dev_pixels.data_ptr(), w, h, k,
+                                            _check_key(key, "key"), _check_key(iv, "iv"),
+                                            dev_public.data_ptr() if dev_public.numel() else None,
+                                            dev_private.data_ptr(),
+                                            host_public.data_ptr() if host_public.numel() else None,
+                                            host_private.data_ptr(), strips, _stream_ptr(dev_pixels.device))
+    _lib.check(rc, "fds_protect_image_host")
+
+
+def restore_image_host(dev_public: torch.Tensor, dev_private: torch.Tensor, dev_pixels: torch.Tensor,
+                       host_pixels: torch.Tensor, key: bytes, iv: bytes, k: int, strips: int = 8) -> None:
+    """fds_restore_image_host: restore on the device, pixels back to the host by strips."""
+    w, h = int(host_pixels.shape[1]), int(host_pixels.shape[0])
+    if host_pixels.is_cuda or not host_pixels.is_contiguous():
+        raise ValueError("host_pixels must be a contiguous CPU tensor")
+    rc = _lib.load().fds_restore_image_host(dev_public.data_ptr() if dev_public.numel() else None,
+                                            dev_private.data_ptr(), dev_pixels.data_ptr(), host_pixels.data_ptr(),
+                                            w, h, k, _check_key(key, "key"), _check_key(iv, "iv"), strips,
+                                            _stream_ptr(dev_pixels.device))
+    _lib.check(rc, "fds_restore_image_host")
+
+
 def public_image(public: torch.Tensor, width: int, height: int, k: int,
                  out: torch.Tensor | None = None) -> torch.Tensor:
     """fds_public_image: the paper-form public fragment, an H x W x 3 uint8 image (private

@@ -606,6 +606,176 @@ int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8
   return run_restore(a, dev, s);
 }
 
+// ---- protect / restore with host buffers: copies overlapped with the kernels, by strips
+namespace {
+struct HostLanes {
+  cudaStream_t in = nullptr, out = nullptr;   // host -> device and device -> host copies
+};
+HostLanes g_lanes[kMaxDevices];
+
+int host_lanes(int dev, HostLanes** lanes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  HostLanes& l = g_lanes[dev];
+  cudaError_t e = cudaSuccess;
+  if (!l.in && (e = cudaStreamCreateWithFlags(&l.in, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream");
+  if (!l.out && (e = cudaStreamCreateWithFlags(&l.out, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream");
+  *lanes = &l;
+  return FDS_OK;
+}
+
+// A strip is a run of block rows, a multiple of 8 of them: its private bytes, bx * 3 * 2 (k+1)
+// per block row, then start on a keystream-block boundary.
+struct Strip {
+  int r0, rows;
+};
+std::vector<Strip> make_strips(int by, int strips) {
+  int rows = (by + strips - 1) / strips;
+  rows = ((rows + 7) / 8) * 8;
+  std::vector<Strip> out;
+  for (int r0 = 0; r0 < by; r0 += rows) out.push_back({r0, by - r0 < rows ? by - r0 : rows});
+  return out;
+}
+
+// the counter block `blocks` keystream blocks after (hi, lo): a 128-bit big-endian addition
+void iv_advance(uint64_t* hi, uint64_t* lo, uint64_t blocks) {
+  const uint64_t l = *lo + blocks;
+  if (l < *lo) ++*hi;
+  *lo = l;
+}
+
+// events recorded while enqueuing; destroyed once enqueued (the runtime keeps them alive
+// until they complete)
+struct EventSet {
+  std::vector<cudaEvent_t> ev;
+  ~EventSet() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  cudaError_t record(cudaStream_t s, cudaEvent_t* out) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    *out = e;
+    return cudaEventRecord(e, s);
+  }
+};
+
+int host_checks(int32_t width, int32_t height, int32_t k, int32_t strips, const void* a, const void* b,
+                const void* c, const void* d, const void* key, const void* iv) {
+  if (bad_dims(width, height)) return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8");
+  if (k < 0 || k > 63) return set_err(FDS_E_INVALID, "k must be in 0..63");
+  if (strips < 1 || strips > 64) return set_err(FDS_E_INVALID, "strips must be in 1..64");
+  if (!a || !b || !c || !d || !key || !iv) return set_err(FDS_E_INVALID, "null pointer argument");
+  return FDS_OK;
+}
+}  // namespace
+
+int fds_protect_image_host(const uint8_t* host_pixels, uint8_t* dev_pixels, int32_t width, int32_t height,
+                           int32_t k, const uint8_t key[16], const uint8_t iv[16], int16_t* dev_public,
+                           uint8_t* dev_private, int16_t* host_public, uint8_t* host_private, int32_t strips,
+                           void* stream) {
+  int rc = host_checks(width, height, k, strips, host_pixels, dev_pixels, dev_private, host_private, key, iv);
+  if (rc) return rc;
+  if (k < 63 && (!dev_public || !host_public)) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(dev_pixels, 8) || misaligned(dev_public, 16) || misaligned(dev_private, 16))
+    return set_err(FDS_E_INVALID, "device pixels must be 8-byte aligned, fragments 16-byte aligned");
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  HostLanes* ln = nullptr;
+  if ((rc = host_lanes(dev, &ln))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t w3 = 3ull * (uint64_t)width, bx = (uint64_t)(width / 8);
+  const uint64_t pub_row = bx * 3ull * (uint64_t)(63 - k), priv_row = bx * 3ull * 2ull * (uint64_t)(k + 1);
+  uint32_t rk[44];
+  expand_key(key, rk);
+  uint64_t hi0, lo0;
+  iv_words(iv, &hi0, &lo0);
+  EventSet evs;
+  cudaEvent_t e0;
+  cudaError_t e = evs.record(s, &e0);   // earlier work on the caller's stream comes first
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ln->in, e0, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ln->out, e0, 0);
+  for (const Strip& st : make_strips(height / 8, strips)) {
+    if (e != cudaSuccess) break;
+    const uint64_t px0 = (uint64_t)st.r0 * 8ull * w3, pxn = (uint64_t)st.rows * 8ull * w3;
+    e = cudaMemcpyAsync(dev_pixels + px0, host_pixels + px0, pxn, cudaMemcpyHostToDevice, ln->in);
+    cudaEvent_t ein, ek;
+    if (e == cudaSuccess) e = evs.record(ln->in, &ein);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ein, 0);
+    if (e != cudaSuccess) break;
+    TileArgs a{};
+    a.pixels_in = dev_pixels + px0;
+    a.pub_out = dev_public ? dev_public + (uint64_t)st.r0 * pub_row : nullptr;
+    a.priv_out = dev_private + (uint64_t)st.r0 * priv_row;
+    fill_geometry(a, width, st.rows * 8, k);
+    std::memcpy(a.rk, rk, sizeof(rk));
+    a.iv_hi = hi0;
+    a.iv_lo = lo0;
+    iv_advance(&a.iv_hi, &a.iv_lo, (uint64_t)st.r0 * priv_row / 16);
+    if ((rc = run_protect(a, dev, s, false))) return rc;
+    e = evs.record(s, &ek);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ln->out, ek, 0);
+    if (e == cudaSuccess && k < 63)
+      e = cudaMemcpyAsync(host_public + (uint64_t)st.r0 * pub_row, a.pub_out, (uint64_t)st.rows * pub_row * 2ull,
+                          cudaMemcpyDeviceToHost, ln->out);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host_private + (uint64_t)st.r0 * priv_row, a.priv_out, (uint64_t)st.rows * priv_row,
+                          cudaMemcpyDeviceToHost, ln->out);
+  }
+  cudaEvent_t ed;
+  if (e == cudaSuccess) e = evs.record(ln->out, &ed);   // the caller's stream completes after the copies
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ed, 0);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "host pipeline");
+}
+
+int fds_restore_image_host(const int16_t* dev_public, const uint8_t* dev_private, uint8_t* dev_pixels,
+                           uint8_t* host_pixels, int32_t width, int32_t height, int32_t k, const uint8_t key[16],
+                           const uint8_t iv[16], int32_t strips, void* stream) {
+  int rc = host_checks(width, height, k, strips, dev_private, dev_pixels, host_pixels, host_pixels, key, iv);
+  if (rc) return rc;
+  if (k < 63 && !dev_public) return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(dev_pixels, 8) || misaligned(dev_public, 16) || misaligned(dev_private, 16))
+    return set_err(FDS_E_INVALID, "device pixels must be 8-byte aligned, fragments 16-byte aligned");
+  int dev = 0;
+  if ((rc = ensure_init(&dev))) return rc;
+  HostLanes* ln = nullptr;
+  if ((rc = host_lanes(dev, &ln))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t w3 = 3ull * (uint64_t)width, bx = (uint64_t)(width / 8);
+  const uint64_t pub_row = bx * 3ull * (uint64_t)(63 - k), priv_row = bx * 3ull * 2ull * (uint64_t)(k + 1);
+  uint32_t rk[44];
+  expand_key(key, rk);
+  uint64_t hi0, lo0;
+  iv_words(iv, &hi0, &lo0);
+  EventSet evs;
+  cudaError_t e = cudaSuccess;
+  for (const Strip& st : make_strips(height / 8, strips)) {
+    const uint64_t px0 = (uint64_t)st.r0 * 8ull * w3, pxn = (uint64_t)st.rows * 8ull * w3;
+    TileArgs a{};
+    a.pub_in = dev_public ? dev_public + (uint64_t)st.r0 * pub_row : nullptr;
+    a.priv_in = dev_private + (uint64_t)st.r0 * priv_row;
+    a.pixels_out = dev_pixels + px0;
+    fill_geometry(a, width, st.rows * 8, k);
+    std::memcpy(a.rk, rk, sizeof(rk));
+    a.iv_hi = hi0;
+    a.iv_lo = lo0;
+    iv_advance(&a.iv_hi, &a.iv_lo, (uint64_t)st.r0 * priv_row / 16);
+    if ((rc = run_restore(a, dev, s))) return rc;
+    cudaEvent_t ek;
+    e = evs.record(s, &ek);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ln->out, ek, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host_pixels + px0, dev_pixels + px0, pxn, cudaMemcpyDeviceToHost, ln->out);
+    if (e != cudaSuccess) break;
+  }
+  cudaEvent_t ed;
+  if (e == cudaSuccess) e = evs.record(ln->out, &ed);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ed, 0);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "host pipeline");
+}
+
 // ---- the paper-form public fragment and the statistics of Sect. 6.6
 int fds_public_image(const int16_t* public_in, int32_t width, int32_t height, int32_t k, uint8_t* image_out,
                      void* stream) {

@@ -1,0 +1,69 @@
+"""Protect / restore with host buffers (fds_protect_image_host / fds_restore_image_host): the
+strip pipeline gives the same bytes as the device entry points, on both sides of the copies."""
+import numpy as np
+import pytest
+
+from oracle import fds as ofds
+from paper_1512_02951_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_02951_gb300 import api as _api, build
+
+    build.build()
+    _api.init(0)
+    return _api
+
+
+def _run(api, img, k, strips, pinned=True):
+    h, w, _ = img.shape
+    key, iv = synth.make_key(w + k), synth.make_iv(h + strips)
+    pub_b, priv_b = api.sizes(w, h, k)
+    host_px = torch.from_numpy(img).pin_memory() if pinned else torch.from_numpy(img.copy())
+    dev_px = torch.empty((h, w, 3), dtype=torch.uint8, device=DEV)
+    dev_pub = torch.empty(pub_b // 2, dtype=torch.int16, device=DEV)
+    dev_priv = torch.empty(max(priv_b, 16), dtype=torch.uint8, device=DEV)
+    host_pub = torch.empty(pub_b // 2, dtype=torch.int16)
+    host_priv = torch.empty(priv_b, dtype=torch.uint8)
+    if pinned:
+        host_pub, host_priv = host_pub.pin_memory(), host_priv.pin_memory()
+    api.protect_image_host(host_px, dev_px, key, iv, k, dev_pub, dev_priv, host_pub, host_priv, strips)
+    out_dev = torch.empty_like(dev_px)
+    host_out = torch.empty((h, w, 3), dtype=torch.uint8)
+    if pinned:
+        host_out = host_out.pin_memory()
+    api.restore_image_host(dev_pub, dev_priv, out_dev, host_out, key, iv, k, strips)
+    torch.cuda.current_stream().synchronize()      # the caller's stream covers every copy
+    want_pub, want_priv = api.protect_image(torch.from_numpy(img).to(DEV), key, iv, k)
+    want_back = api.restore_image(want_pub, want_priv, w, h, k, key, iv)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_pub.numpy(), want_pub.reshape(-1).cpu().numpy())
+    assert host_priv.numpy().tobytes() == want_priv.cpu().numpy().tobytes()[:priv_b]
+    assert torch.equal(dev_pub, want_pub.reshape(-1)) and np.array_equal(host_out.numpy(), want_back.cpu().numpy())
+    return host_pub.numpy(), host_priv.numpy().tobytes(), host_out.numpy(), key, iv
+
+
+@pytest.mark.parametrize("k", [0, 5, 17, 63])
+@pytest.mark.parametrize("strips", [1, 2, 5])
+def test_strips_match_device_entry_points(api, k, strips):
+    # 17 block rows: strips of 8, 8, 1 rows (or one strip), so a strip ends mid-image
+    _run(api, synth.make_image(136, 136, 3 * k + strips), k, strips)
+
+
+def test_against_the_oracle_and_pageable_memory(api):
+    img = synth.make_image(72, 200, 5)
+    pub, priv, back, key, iv = _run(api, img, 5, 3, pinned=False)
+    want_pub, want_priv = ofds.protect(img, key, iv, 5)
+    assert np.array_equal(pub, want_pub.reshape(-1)) and priv == want_priv
+    assert np.array_equal(back, ofds.restore(want_pub, want_priv, key, iv, 5, 72, 200))
+
+
+def test_full_size(api):
+    _run(api, synth.make_image(4096, 4096, 2), 5, 8)
