@@ -679,7 +679,9 @@ def packed_arm(args):
     build.build()
     api.init(0)
     dev = torch.device("cuda", 0)
-    img = torch.from_numpy(synth.make_image(WIDTH, HEIGHT, IMG_SEED)).to(dev)
+    img_np = synth.make_image(WIDTH, HEIGHT, IMG_SEED)
+    img = torch.from_numpy(img_np).to(dev)
+    img_np = img_np.astype(np.float64)
     key, iv = synth.make_key(KEY_SEED), synth.make_iv(IV_SEED)
     px_bytes = WIDTH * HEIGHT * 3
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -716,7 +718,11 @@ def packed_arm(args):
         p_ms = timed(lambda: api.protect_image_packed(img, key, iv, K_SEL, form, scratch, pub, priv))
         r_ms = timed(lambda: api.restore_image_packed(pub, priv[:priv_b], WIDTH, HEIGHT, K_SEL, key, iv, form,
                                                       scratch, out))
+        back = out.cpu().numpy().astype(np.float64)
+        mse = float(np.mean((back - img_np) ** 2))
         res[f"packed{form}"] = {"protect_ms": round(p_ms, 5), "restore_ms": round(r_ms, 5),
+                                "restore_psnr_db": round(10.0 * np.log10(255.0 ** 2 / mse), 3) if mse else None,
+                                "restore_exact_fraction": round(float((back == img_np).mean()), 5),
                                 "public_bytes": pub_b, "private_bytes": priv_b,
                                 "stored_fraction_of_pixels": round((pub_b + priv_b) / px_bytes, 4),
                                 "private_fraction_of_pixels": round(priv_b / px_bytes, 4)}

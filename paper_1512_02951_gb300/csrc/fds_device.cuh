@@ -117,6 +117,78 @@ __device__ __forceinline__ float dct8_rat_w(float (&x)[8]) {
   return pass_weight(s, d);
 }
 
+// ---- the same butterflies on pairs of independent columns (packed f32x2 arithmetic); every
+// lane performs exactly the scalar operations, so the results are bit-identical
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float k) { return __fmul2_rn(a, make_float2(k, k)); }
+__device__ __forceinline__ float2 fma2(float2 a, float k, float2 c) { return __ffma2_rn(a, make_float2(k, k), c); }
+
+template <bool RAT_UNSCALED, bool IRR_LAMBDA>
+__device__ __forceinline__ void dct8_sd2(const float2 (&s)[4], const float2 (&d)[4], float2 (&x)[8]) {
+  constexpr double m = IRR_LAMBDA ? kLambda : 1.0;
+  constexpr float a2 = (float)(0.5 * m * kC2), a6 = (float)(0.5 * m * kC6);
+  constexpr float h1 = (float)(0.5 * m * kC1), h3 = (float)(0.5 * m * kC3);
+  constexpr float h5 = (float)(0.5 * m * kC5), h7 = (float)(0.5 * m * kC7);
+  constexpr float lam = (float)kLambda;
+  const float2 e0 = add2(s[0], s[3]), e1 = add2(s[1], s[2]), f0 = sub2(s[0], s[3]), f1 = sub2(s[1], s[2]);
+  if (RAT_UNSCALED) {
+    x[0] = add2(e0, e1);
+    x[4] = sub2(e0, e1);
+  } else {
+    x[0] = fma2(e0, lam, mul2(e1, lam));
+    x[4] = fma2(e0, lam, mul2(e1, -lam));
+  }
+  x[2] = fma2(f0, a2, mul2(f1, a6));
+  x[6] = fma2(f0, a6, mul2(f1, -a2));
+  x[1] = fma2(d[3], h7, fma2(d[2], h5, fma2(d[1], h3, mul2(d[0], h1))));
+  x[3] = fma2(d[3], -h5, fma2(d[2], -h1, fma2(d[1], -h7, mul2(d[0], h3))));
+  x[5] = fma2(d[3], h3, fma2(d[2], h7, fma2(d[1], -h1, mul2(d[0], h5))));
+  x[7] = fma2(d[3], -h1, fma2(d[2], h3, fma2(d[1], -h5, mul2(d[0], h7))));
+}
+
+template <bool RAT_UNSCALED, bool IRR_LAMBDA>
+__device__ __forceinline__ void dct8_2(float2 (&x)[8]) {
+  const float2 s[4] = {add2(x[0], x[7]), add2(x[1], x[6]), add2(x[2], x[5]), add2(x[3], x[4])};
+  const float2 d[4] = {sub2(x[0], x[7]), sub2(x[1], x[6]), sub2(x[2], x[5]), sub2(x[3], x[4])};
+  dct8_sd2<RAT_UNSCALED, IRR_LAMBDA>(s, d, x);
+}
+
+// dct8_rat_w on two exact-integer columns at once; returns the sum of both error weights
+__device__ __forceinline__ float dct8_rat_w2(float2 (&x)[8]) {
+  const float2 s[4] = {add2(x[0], x[7]), add2(x[1], x[6]), add2(x[2], x[5]), add2(x[3], x[4])};
+  const float2 d[4] = {sub2(x[0], x[7]), sub2(x[1], x[6]), sub2(x[2], x[5]), sub2(x[3], x[4])};
+  dct8_sd2<true, true>(s, d, x);
+  const float wx = ((fabsf(d[0].x) + fabsf(d[1].x)) + (fabsf(d[2].x) + fabsf(d[3].x))) +
+                   (fabsf(s[0].x - s[3].x) + fabsf(s[1].x - s[2].x));
+  const float wy = ((fabsf(d[0].y) + fabsf(d[1].y)) + (fabsf(d[2].y) + fabsf(d[3].y))) +
+                   (fabsf(s[0].y - s[3].y) + fabsf(s[1].y - s[2].y));
+  return wx + wy;
+}
+
+// idct8 on two independent columns at once (bit-identical per lane)
+__device__ __forceinline__ void idct8_2(float2 (&x)[8]) {
+  constexpr float lam = (float)kLambda;
+  constexpr float c2 = (float)(0.5 * kC2), c6 = (float)(0.5 * kC6);
+  constexpr float h1 = (float)(0.5 * kC1), h3 = (float)(0.5 * kC3);
+  constexpr float h5 = (float)(0.5 * kC5), h7 = (float)(0.5 * kC7);
+  const float2 a = fma2(x[0], lam, mul2(x[4], lam)), b = fma2(x[0], lam, mul2(x[4], -lam));
+  const float2 t1 = fma2(x[2], c2, mul2(x[6], c6)), t2 = fma2(x[2], c6, mul2(x[6], -c2));
+  const float2 e0 = add2(a, t1), e1 = add2(b, t2), e2 = sub2(b, t2), e3 = sub2(a, t1);
+  const float2 o0 = fma2(x[7], h7, fma2(x[5], h5, fma2(x[3], h3, mul2(x[1], h1))));
+  const float2 o1 = fma2(x[7], -h5, fma2(x[5], -h1, fma2(x[3], -h7, mul2(x[1], h3))));
+  const float2 o2 = fma2(x[7], h3, fma2(x[5], h7, fma2(x[3], -h1, mul2(x[1], h5))));
+  const float2 o3 = fma2(x[7], -h1, fma2(x[5], h3, fma2(x[3], -h5, mul2(x[1], h7))));
+  x[0] = add2(e0, o0);
+  x[7] = sub2(e0, o0);
+  x[1] = add2(e1, o1);
+  x[6] = sub2(e1, o1);
+  x[2] = add2(e2, o2);
+  x[5] = sub2(e2, o2);
+  x[3] = add2(e3, o3);
+  x[4] = sub2(e3, o3);
+}
+
 // Inverse: X (orthonormal coefficients) -> x_n = sum_k b_k(n) X_k.
 __device__ __forceinline__ void idct8(float (&x)[8]) {
   constexpr float lam = (float)kLambda;

@@ -6,9 +6,11 @@
 //   A. the tile's pixels (prefetched with cp.async during the previous tile) are in shared
 //      memory; the previous tile's fragments leave through bulk (TMA engine) stores and the
 //      next tile's pixels start loading
-//   1. per channel-block: row then column float32 butterflies; every coefficient rounded to
-//      int16 and written to the public or private staging area at its zigzag position;
-//      coefficients within the float32 error guard of a half-integer are queued
+//   1. per channel-block: row then column float32 butterflies (the column pass and the
+//      rounding on pairs of columns with packed f32x2 instructions, bit-identical per lane);
+//      every coefficient rounded to int16 and written to the public or private staging area
+//      at its zigzag position; coefficients within the float32 error guard of a half-integer
+//      are queued
 //   B. 2. queued coefficients are re-decided exactly (integer coordinates in Z[cos(pi/16)])
 //   C. 3. the public fragment leaves (bulk store) while AES-128-CTR encrypts the private
 //      staging area, one thread per 16-byte keystream block
@@ -242,6 +244,13 @@ __device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
   cp_async_commit();
 }
 
+// column pairs of the packed column pass: (0, 4), (1, 2), (3, 5), (6, 7)
+__host__ __device__ constexpr int pair_of(int v) { return (v == 0 || v == 4) ? 0 : (v < 3 ? 1 : ((v == 3 || v == 5) ? 2 : 3)); }
+__host__ __device__ constexpr int pair_lane(int v) { return (v == 4 || v == 2 || v == 5 || v == 7) ? 1 : 0; }
+__host__ __device__ constexpr int pair_col(int j, int l) {
+  return j == 0 ? (l ? 4 : 0) : (j == 1 ? (l ? 2 : 1) : (j == 2 ? (l ? 5 : 3) : (l ? 7 : 6)));
+}
+
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
 // from the kernel parameters, which AES then takes as constant-bank operands).
 // PACK: 0 = int16 fragments; 11 or 8 = packed streams (one image)
@@ -300,7 +309,9 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     int16_t* privst = reinterpret_cast<int16_t*>(smem + kSmemStage + kTileCb * 2 * npub);
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
     if (b < nb) {
-      float f[8][8];
+      // row outputs kept as pairs of columns (0, 4), (1, 2), (3, 5), (6, 7), so that the
+      // column pass runs on two columns per packed f32x2 instruction
+      float2 P[8][4];
       float V = 0.0f, W = 0.0f;   // error weights of the row passes and of columns 0, 4
 #pragma unroll
       for (int y = 0; y < 8; ++y) {
@@ -312,28 +323,38 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
           const int byte = 3 * x;
           X[x] = __int_as_float(__byte_perm(w[byte >> 2], 0x4B000000u, 0x7440u | (byte & 3)));
         }
-        V += dct8_row_bytes_w(X, f[y]);
+        float fr[8];
+        V += dct8_row_bytes_w(X, fr);
+        P[y][0] = make_float2(fr[0], fr[4]);
+        P[y][1] = make_float2(fr[1], fr[2]);
+        P[y][2] = make_float2(fr[3], fr[5]);
+        P[y][3] = make_float2(fr[6], fr[7]);
       }
-      // columns; columns 0 and 4 hold unscaled (exact integer) row outputs
+      {   // columns 0 and 4 hold unscaled (exact integer) row outputs
+        float2 col[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        float col[8];
+        for (int y = 0; y < 8; ++y) col[y] = P[y][0];
+        W += dct8_rat_w2(col);
 #pragma unroll
-        for (int y = 0; y < 8; ++y) col[y] = f[y][v];
-        if (v == 0 || v == 4)
-          W += dct8_rat_w(col);
-        else
-          dct8<false, false>(col);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) f[u][v] = col[u];
+        for (int u = 0; u < 8; ++u) P[u][0] = col[u];
       }
+#pragma unroll
+      for (int j = 1; j < 4; ++j) {
+        float2 col[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) col[y] = P[y][j];
+        dct8_2<false, false>(col);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) P[u][j] = col[u];
+      }
+#define F(u, v) (pair_lane(v) ? P[u][pair_of(v)].y : P[u][pair_of(v)].x)
       if (DEBUG) {
         float* out = a.dbg_coefs + ((uint64_t)sl->local * kTileBlocks * 3 + cb) * 64;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
-            float val = f[u][v];
+            float val = F(u, v);
             if (u == 0 && v == 0)
               val = (val + 8192.0f) * 0.125f;
             else if ((u == 0 || u == 4) && (v == 0 || v == 4))
@@ -342,36 +363,47 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
           }
       } else {
         // rounding: the four rational positions exactly in integers; the rest to nearest in
-        // float32, residual checked against the guard (near ties marked in a 64-bit mask)
+        // float32 (two at a time), residual checked against the guard (near ties marked in a
+        // 64-bit mask)
         int16_t* pub_cb = pubst + cb * npub;
         int16_t* priv_cb = privst + cb * (k + 1);
         uint32_t mlo = 0, mhi = 0;
         const float thr = 0.5f - fminf(fmaf(V, kGuardV, fmaf(W, kGuardW, kGuardU)), kGuardFwd);
+        auto put = [&](int u, int v, uint32_t q) {
+          const int z = zigzag_of(u, v);
+          if (z <= k)
+            priv_cb[z] = (int16_t)q;
+          else
+            pub_cb[z - k - 1] = (int16_t)q;
+        };
+        auto mark = [&](int u, int v) {
+          if (8 * u + v < 32)
+            mlo |= 1u << (8 * u + v);
+          else
+            mhi |= 1u << (8 * u + v - 32);
+        };
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const int z = zigzag_of(u, v);
-            uint32_t q;
-            if ((u == 0 || u == 4) && (v == 0 || v == 4)) {
-              const int T = __float_as_int(f[u][v] + kMagic) - kMagicBits;  // 8 F, exact
-              q = (uint32_t)((u == 0 && v == 0) ? ((T + 4) >> 3) + 1024 : (T + 4 - (T < 0 ? 1 : 0)) >> 3);
-            } else {
-              const float yv = f[u][v] + kMagic;
-              q = __float_as_uint(yv);                 // low 16 bits: the int16 result
-              if (fabsf(f[u][v] - (yv - kMagic)) > thr) {
-                if (8 * u + v < 32)
-                  mlo |= 1u << (8 * u + v);
-                else
-                  mhi |= 1u << (8 * u + v - 32);
+          for (int j = 0; j < 4; ++j) {
+            if ((u == 0 || u == 4) && j == 0) {
+#pragma unroll
+              for (int l = 0; l < 2; ++l) {
+                const int v = pair_col(0, l);
+                const int T = __float_as_int(F(u, v) + kMagic) - kMagicBits;  // 8 F, exact
+                put(u, v, (uint32_t)((u == 0 && v == 0) ? ((T + 4) >> 3) + 1024 : (T + 4 - (T < 0 ? 1 : 0)) >> 3));
               }
+            } else {
+              const float2 yv = add2(P[u][j], make_float2(kMagic, kMagic));
+              const float2 r = sub2(P[u][j], add2(yv, make_float2(-kMagic, -kMagic)));
+              put(u, pair_col(j, 0), __float_as_uint(yv.x));   // low 16 bits: the int16 result
+              put(u, pair_col(j, 1), __float_as_uint(yv.y));
+              if (fabsf(r.x) > thr) mark(u, pair_col(j, 0));
+              if (fabsf(r.y) > thr) mark(u, pair_col(j, 1));
             }
-            if (z <= k)
-              priv_cb[z] = (int16_t)q;
-            else
-              pub_cb[z - k - 1] = (int16_t)q;
           }
         }
+#undef F
         uint64_t mask = ((uint64_t)mhi << 32) | mlo;
         while (mask) {
           const int pos = __ffsll((long long)mask) - 1;

@@ -6,9 +6,10 @@
 // launch); per tile (see fds_tile.cuh for the decomposition):
 //   A. the tile's fragments are in shared memory, already decrypted; the next tile's start
 //      loading (one bulk copy per fragment range, or cp.async pieces)
-//   1. per channel-block: column then row float32 inverse butterflies, round + clamp, bytes
-//      into the interleaved pixel tile; values within the float32 error guard of a
-//      half-integer are queued
+//   1. per channel-block: column then row float32 inverse butterflies (the column pass and
+//      the rounding on pairs with packed f32x2 instructions, bit-identical per lane), round +
+//      clamp, bytes into the interleaved pixel tile; values within the float32 error guard of
+//      a half-integer are queued
 //   B. 2. queued pixels are re-decided exactly (integer coordinates in Z[cos(pi/16)]) by the
 //      last threads while the first ones decrypt the next tile's private range in place
 //      (AES-128-CTR)
@@ -176,45 +177,61 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     if (b < nb) {
       const int16_t* pub_cb = pubst + cb * npub;
       const int16_t* priv_cb = privst + cb * (k + 1);
-      float f[8][8];
+      // coefficients as pairs of adjacent columns: the column pass runs on two columns per
+      // packed f32x2 instruction
+      float2 G[8][4];
       float l1 = 0.0f;  // sum |F|, exact (integers below 2^24)
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int z = zigzag_of(u, v);
-          const int q = z <= k ? priv_cb[z] : pub_cb[z - k - 1];
-          f[u][v] = __int_as_float(kMagicBits + q) - kMagic;
-          l1 += fabsf(f[u][v]);
+        for (int j = 0; j < 4; ++j) {
+          const int z0 = zigzag_of(u, 2 * j), z1 = zigzag_of(u, 2 * j + 1);
+          const int q0 = z0 <= k ? priv_cb[z0] : pub_cb[z0 - k - 1];
+          const int q1 = z1 <= k ? priv_cb[z1] : pub_cb[z1 - k - 1];
+          G[u][j] = add2(make_float2(__int_as_float(kMagicBits + q0), __int_as_float(kMagicBits + q1)),
+                         make_float2(-kMagic, -kMagic));
+          l1 += fabsf(G[u][j].x);
+          l1 += fabsf(G[u][j].y);
         }
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        float col[8];
+      for (int j = 0; j < 4; ++j) {
+        float2 col[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) col[u] = f[u][v];
-        idct8(col);
+        for (int u = 0; u < 8; ++u) col[u] = G[u][j];
+        idct8_2(col);
 #pragma unroll
-        for (int y = 0; y < 8; ++y) f[y][v] = col[y];
+        for (int y = 0; y < 8; ++y) G[y][j] = col[y];
       }
-#pragma unroll
-      for (int y = 0; y < 8; ++y) idct8(f[y]);
       const float thr = 0.5f - l1 * kGuardInvScale;
       uint8_t* out = pix + b * 24 + c;
       uint32_t mlo = 0, mhi = 0;
 #pragma unroll
-      for (int y = 0; y < 8; ++y)
+      for (int y = 0; y < 8; ++y) {
+        float row[8];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          const float pc = fminf(fmaxf(f[y][x], 0.0f), 255.0f);
-          const float yv = pc + kMagic;
-          if (fabsf(pc - (yv - kMagic)) > thr) {
-            if (8 * y + x < 32)
-              mlo |= 1u << (8 * y + x);
-            else
-              mhi |= 1u << (8 * y + x - 32);
-          }
-          out[y * kRowBytes + 3 * x] = (uint8_t)__float_as_uint(yv);
+        for (int j = 0; j < 4; ++j) {
+          row[2 * j] = G[y][j].x;
+          row[2 * j + 1] = G[y][j].y;
         }
+        idct8(row);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 pc = make_float2(fminf(fmaxf(row[2 * j], 0.0f), 255.0f), fminf(fmaxf(row[2 * j + 1], 0.0f), 255.0f));
+          const float2 yv = add2(pc, make_float2(kMagic, kMagic));
+          const float2 r = sub2(pc, add2(yv, make_float2(-kMagic, -kMagic)));
+#pragma unroll
+          for (int l = 0; l < 2; ++l) {
+            const int x = 2 * j + l;
+            if (fabsf(l ? r.y : r.x) > thr) {
+              if (8 * y + x < 32)
+                mlo |= 1u << (8 * y + x);
+              else
+                mhi |= 1u << (8 * y + x - 32);
+            }
+            out[y * kRowBytes + 3 * x] = (uint8_t)__float_as_uint(l ? yv.y : yv.x);
+          }
+        }
+      }
       uint64_t mask = ((uint64_t)mhi << 32) | mlo;
       while (mask) {
         const int pos = __ffsll((long long)mask) - 1;
