@@ -735,7 +735,7 @@ def packed_arm(args):
             "config": {"workload": f"{WIDTH}x{HEIGHT} RGB uint8, k={K_SEL}: int16 vs 11-bit vs 8-bit "
                                    "fragment storage", "l2": "256 MB buffer written between timed launches"},
             "results": res,
-            "gpu_launches": args.steps * 14}   # int16 2 + 2 forms x (protect 3 + restore 3)
+            "gpu_launches": args.steps * 6}   # int16 2 + 2 forms x (protect 1 + restore 1)
     print(json.dumps(line), flush=True)
 
 

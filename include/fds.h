@@ -239,10 +239,13 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
  * channel-blocks in [by][bx][c] order, each with its fields in fragment order (zigzag k+1..63,
  * resp. 0..k); the last byte is zero-padded.  The packed private stream is AES-128-CTR
  * encrypted from the IV like the int16 one.
- * Protect is one launch (the transform packs and encrypts each tile in shared memory); restore
- * decrypts, unpacks to int16 in scratch and runs the restore kernel.
+ * Protect is one launch (the transform packs and encrypts each tile in shared memory); so is
+ * restore when the packed public stream is 8-byte aligned (each tile's packed parts land in
+ * shared memory, are decrypted and unpacked there), else it decrypts, unpacks to int16 in
+ * scratch and runs the restore kernel.
  * fds_sizes_packed gives the packed fragment sizes and the device scratch restore needs (the
- * int16 fragments and the decrypted packed stream; protect does not touch scratch).  Arguments
+ * int16 fragments and the decrypted packed stream; protect, and restore of an 8-byte aligned
+ * public stream, do not touch it).  Arguments
  * otherwise as fds_protect_image / fds_restore_image; private and scratch 16-byte aligned, the
  * packed public fragment at any alignment.  scratch: device, owned by the caller, overwritten. */
 #define FDS_PACK_11 11

@@ -22,7 +22,6 @@
 namespace fds {
 
 constexpr int kPackThreads = 256;
-constexpr int kDcBits = 11;
 
 __device__ __forceinline__ int ac_value(uint32_t code, int w) {
   const int mag = (int)(code & ((1u << (w - 1)) - 1u));

@@ -60,7 +60,6 @@ __device__ __forceinline__ void store_private(const TileSlot* sl, const uint8_t*
 }
 
 // ---- packed storage ---------------------------------------------------------------------
-constexpr int kDcBits = 11;
 
 // field code of AC value v in W bits: sign-magnitude, the magnitude saturated to W - 1 bits
 template <int W>
@@ -161,16 +160,6 @@ __device__ __forceinline__ void pack_tile(uint8_t* st, int nb, int k) {
   }
 }
 
-// bytes of a tile's packed public / private part and their offsets in the image's streams
-// (a full tile: 24 (63 - k) W and 24 (11 + k W) bytes)
-template <int W>
-__device__ __forceinline__ void packed_extent(const TileSlot* sl, bool priv, uint64_t& off, int& bytes) {
-  const int k = sl->k;
-  const int per_cb = priv ? kDcBits + k * W : (63 - k) * W;   // bits per channel-block
-  off = (uint64_t)sl->local * 24ull * (uint64_t)per_cb;
-  bytes = (3 * sl->nb * per_cb + 7) >> 3;
-}
-
 // the packed public part of slot sl (at st) to global memory (all threads): one bulk store
 // when its destination is 16-byte aligned, else 4-byte or byte stores
 template <int W>
@@ -209,27 +198,6 @@ __device__ __forceinline__ void store_private_packed(const TileSlot* sl, const u
   for (int i = t; i < (bytes >> 2); i += kThreads)
     reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
   if (t < (bytes & 3)) dst[(bytes & ~3) + t] = src[(bytes & ~3) + t];
-}
-
-// AES-128-CTR over the tile's packed private part (words at w, stream bytes [off, off +
-// bytes), off a multiple of 4): one thread per keystream block the part overlaps; a block
-// that straddles two tiles is generated by both, each XORing its own words
-__device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int bytes, const TileSlot* sl,
-                                                const uint32_t* rk, const uint32_t* Ts) {
-  const uint64_t b0 = off >> 4;
-  const int nblk = (int)(((off + (uint64_t)bytes + 15) >> 4) - b0);
-  const int nw = (bytes + 3) >> 2;
-  const int skew = (int)((off & 15) >> 2);
-  for (int i = threadIdx.x; i < nblk; i += kThreads) {
-    uint32_t s[4];
-    ctr_block(sl->iv_hi, sl->iv_lo, b0 + i, s);
-    aes128_encrypt(s, rk, Ts);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int wi = 4 * i + m - skew;
-      if (wi >= 0 && wi < nw) w[wi] ^= s[m];
-    }
-  }
 }
 
 // cp.async the pixels of slot sl into pixel tile pix (all threads)

@@ -17,6 +17,11 @@
 //      the tile's rows are contiguous and 16-byte aligned, else 8-byte stores.  The pixel tile
 //      is double-buffered so the bulk stores overlap the next tile.
 //
+// Packed storage (PACK = 11 or 8 bits per AC field, Sect. 6.4.3): the tile's part of the two
+// packed streams lands in a separate shared-memory area (bulk copies when 16-byte aligned,
+// else 8-byte cp.async pieces), its private bytes are decrypted there and both parts are
+// unpacked into the int16 staging area, all one tile ahead, before the transform reads it.
+//
 // Public-image form (PUBIMG; the paper's public fragment as an image, Sect. 6.5.1 Fig. 10):
 // the same kernel with the private positions "padded with zeros" -- the private staging
 // holds the constant (1024, 0, .., 0) per channel-block (DC 8 x 128: the zero-mean block
@@ -33,6 +38,136 @@ constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemBar = kSmemSlot + 3 * kSlotBytes;         // 2 mbarriers (staging areas)
 constexpr int kSmemMisc = kSmemBar + 16;
 constexpr int kSmemBytes = kSmemMisc + 32;
+// packed storage: one landing area for a tile's packed public and private parts, 24 (63 w + 11)
+// bytes at most (w = 11) plus 16 for aligning the private part
+constexpr int kLandBytes = 24 * (63 * 11 + 11) + 32;
+constexpr int kSmemLand = kSmemBytes;
+constexpr int kSmemBytesPacked = kSmemLand + kLandBytes;
+
+// ---- packed storage: land, decrypt, unpack one tile
+template <int W>
+__device__ __forceinline__ int land_private_offset(int k) {
+  return ((24 * (63 - k) * W) + 15) & ~15;
+}
+// true if both packed parts of slot sl's tile arrive as one bulk copy each
+template <int W>
+__device__ __forceinline__ bool packed_bulk(const TileSlot* sl) {
+  uint64_t po, vo;
+  int pb, vb;
+  packed_extent<W>(sl, false, po, pb);
+  packed_extent<W>(sl, true, vo, vb);
+  return ((reinterpret_cast<uintptr_t>(sl->pub_in + po) | reinterpret_cast<uintptr_t>(sl->priv_in + vo) |
+           (uintptr_t)pb | (uintptr_t)vb) & 15) == 0;
+}
+// the packed parts of slot sl's tile into the landing area (all threads; thread 0 issues the
+// bulk copies); the streams are 8-byte aligned, so are the tiles' offsets
+template <int W>
+__device__ __forceinline__ void load_packed(const TileSlot* sl, uint8_t* land, uint64_t* bar) {
+  const int t = threadIdx.x;
+  uint64_t po, vo;
+  int pb, vb;
+  packed_extent<W>(sl, false, po, pb);
+  packed_extent<W>(sl, true, vo, vb);
+  const uint8_t* psrc = sl->pub_in + po;
+  const uint8_t* vsrc = sl->priv_in + vo;
+  uint8_t* vdst = land + land_private_offset<W>(sl->k);
+  if (packed_bulk<W>(sl)) {
+    if (t == 0) {
+      mbar_expect_tx(bar, (uint32_t)(pb + vb));
+      if (pb) bulk_load(land, psrc, (uint32_t)pb, bar);
+      if (vb) bulk_load(vdst, vsrc, (uint32_t)vb, bar);
+    }
+    return;
+  }
+  const int p8 = pb >> 3, v8 = vb >> 3;
+  for (int i = t; i < p8 + v8; i += kThreads) {
+    if (i < p8)
+      cp_async8(land + 8 * i, psrc + 8 * i);
+    else
+      cp_async8(vdst + 8 * (i - p8), vsrc + 8 * (i - p8));
+  }
+  if (t < (pb & 7)) land[(pb & ~7) + t] = psrc[(pb & ~7) + t];
+  if (t < (vb & 7)) vdst[(vb & ~7) + t] = vsrc[(vb & ~7) + t];
+  cp_async_commit();
+}
+template <int W>
+__device__ __forceinline__ void wait_packed(const TileSlot* sl, uint64_t* bar, uint32_t& phase, int& lost) {
+  if (packed_bulk<W>(sl)) {
+    if (!mbar_wait(bar, phase)) ++lost;
+    phase ^= 1u;
+  } else {
+    cp_async_wait_all();
+  }
+}
+// AES-128-CTR over the landed private part (all threads; a barrier must follow)
+template <int W>
+__device__ __forceinline__ void decrypt_packed(const TileSlot* sl, uint8_t* land, const uint32_t* rk,
+                                               const uint32_t* Ts) {
+  uint64_t vo;
+  int vb;
+  packed_extent<W>(sl, true, vo, vb);
+  ctr_tile_packed(reinterpret_cast<uint32_t*>(land + land_private_offset<W>(sl->k)), vo, vb, sl, rk, Ts);
+}
+// the landed (decrypted) parts -> int16 staging st, public [cb][63 - k], private [cb][k + 1]
+// (all threads): a public thread unpacks 32 fields (W words), a private thread one
+// channel-block (11 + k W bits)
+template <int W>
+__device__ __forceinline__ void unpack_tile(const TileSlot* sl, const uint8_t* land, uint8_t* st) {
+  const int t = threadIdx.x;
+  const int k = sl->k, nb = sl->nb, npub = 63 - k;
+  const int nf = 3 * nb * npub, ngroups = (nf + 31) >> 5;
+  const uint32_t* pw = reinterpret_cast<const uint32_t*>(land);
+  int16_t* pub16 = reinterpret_cast<int16_t*>(st);
+  for (int g = t; g < ngroups; g += kThreads) {
+    uint32_t word[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) word[j] = pw[W * g + j];
+    int v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int b = W * i;
+      uint32_t c = word[b >> 5] >> (b & 31);
+      if ((b & 31) + W > 32) c |= word[(b >> 5) + 1] << (32 - (b & 31));
+      const int mag = (int)(c & ((1u << (W - 1)) - 1u));
+      v[i] = (c >> (W - 1)) & 1u ? -mag : mag;
+    }
+    const int f0 = 32 * g;
+    if (f0 + 32 <= nf) {
+      uint4* dst = reinterpret_cast<uint4*>(pub16 + f0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t u[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          u[m] = ((uint32_t)v[8 * q + 2 * m] & 0xffffu) | ((uint32_t)v[8 * q + 2 * m + 1] << 16);
+        dst[q] = make_uint4(u[0], u[1], u[2], u[3]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (f0 + i < nf) pub16[f0 + i] = (int16_t)v[i];
+    }
+  }
+  if (t < 3 * nb) {
+    const uint32_t* vw = reinterpret_cast<const uint32_t*>(land + land_private_offset<W>(k));
+    int16_t* dst = reinterpret_cast<int16_t*>(st + kTileCb * 2 * npub) + t * (k + 1);
+    int pos = t * (kDcBits + k * W);
+    for (int z = 0; z <= k; ++z) {
+      const int fw = z == 0 ? kDcBits : W;
+      const int sh = pos & 31;
+      uint32_t c = vw[pos >> 5] >> sh;
+      if (sh + fw > 32) c |= vw[(pos >> 5) + 1] << (32 - sh);
+      c &= (1u << fw) - 1u;
+      if (z == 0) {
+        dst[0] = (int16_t)c;
+      } else {
+        const int mag = (int)(c & ((1u << (W - 1)) - 1u));
+        dst[z] = (int16_t)((c >> (W - 1)) & 1u ? -mag : mag);
+      }
+      pos += fw;
+    }
+  }
+}
 
 // gather the 64 int16 coefficients of tile channel-block cb in zigzag order, two per word
 __device__ __forceinline__ void gather_coefs(const int16_t* pubst, const int16_t* privst, int cb,
@@ -109,7 +244,7 @@ __device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint
 
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
 // from the kernel parameters, which AES then takes as constant-bank operands)
-template <int K, bool BATCH, bool PUBIMG = false>
+template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) uint32_t Ts[1024];                // AES T-tables
@@ -147,10 +282,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     }
   }
   __syncthreads();
-  load_fragments<PUBIMG>(slot(0), stage(0), bars);
-  wait_fragments<PUBIMG>(slot(0), bars, phase[0], lost);
-  __syncthreads();
-  if (!PUBIMG && !a.plain_private) decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
+  uint8_t* land = smem + kSmemLand;   // PACK only
+  if constexpr (PACK != 0) {
+    load_packed<PACK>(slot(0), land, bars);
+    wait_packed<PACK>(slot(0), bars, phase[0], lost);
+    __syncthreads();
+    decrypt_packed<PACK>(slot(0), land, a.rk, Ts);
+    __syncthreads();
+    unpack_tile<PACK>(slot(0), land, stage(0));
+  } else {
+    load_fragments<PUBIMG>(slot(0), stage(0), bars);
+    wait_fragments<PUBIMG>(slot(0), bars, phase[0], lost);
+    __syncthreads();
+    if (!PUBIMG && !a.plain_private) decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
+  }
   int esc = 0;
   bool fail = false;
   for (int it = 0;; ++it) {
@@ -167,7 +312,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     }
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
-    if (nxt < ntiles) load_fragments<PUBIMG>(slot((it + 1) % 3), stage(buf ^ 1), bars + (buf ^ 1));
+    if (nxt < ntiles) {
+      if constexpr (PACK != 0)
+        load_packed<PACK>(slot((it + 1) % 3), land, bars + (buf ^ 1));
+      else
+        load_fragments<PUBIMG>(slot((it + 1) % 3), stage(buf ^ 1), bars + (buf ^ 1));
+    }
     const int k = K >= 0 ? K : sl->k;
     const int npub = 63 - k;
     const int nb = sl->nb;
@@ -249,7 +399,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         }
       }
     }
-    if (nxt < ntiles) wait_fragments<PUBIMG>(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
+    if (nxt < ntiles) {
+      if constexpr (PACK != 0)
+        wait_packed<PACK>(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
+      else
+        wait_fragments<PUBIMG>(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
+    }
     __syncthreads();                                                       // B
     {
       // queued pixels (from the last thread down) re-decided exactly while the first threads
@@ -268,8 +423,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       }
       if (t == 0) misc[1] += misc[0];
     }
-    if (!PUBIMG && nxt < ntiles && !a.plain_private)
+    if constexpr (PACK != 0) {
+      if (nxt < ntiles) {
+        decrypt_packed<PACK>(slot((it + 1) % 3), land, a.rk, Ts);
+        __syncthreads();                                                   // B2
+        unpack_tile<PACK>(slot((it + 1) % 3), land, stage(buf ^ 1));
+      }
+    } else if (!PUBIMG && nxt < ntiles && !a.plain_private) {
       decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
+    }
     fence_proxy_async();                                  // pixel writes before the bulk stores
     __syncthreads();                                                       // C
     {
@@ -310,21 +472,28 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
   }
 }
 
-template <int K, bool BATCH, bool PUBIMG = false>
+template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
-  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG>, kSmemBytes, attr);
+  constexpr int smem = PACK ? kSmemBytesPacked : kSmemBytes;
+  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG, PACK>, smem, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
   const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
-  if (grid > 0) restore_kernel<K, BATCH, PUBIMG><<<grid, kThreads, kSmemBytes, s>>>(a);
+  if (grid > 0) restore_kernel<K, BATCH, PUBIMG, PACK><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile;
 // a.public_image (one image) selects the public-image form
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
+  if (a.pack) {   // one image, packed streams in pub_in / priv_in
+    if (a.images || a.k < 0 || a.public_image || (a.pack != 11 && a.pack != 8)) return cudaErrorInvalidValue;
+    if (a.pack == 11) return a.k == 5 ? launch_k<5, false, false, 11>(a, s, sms, per_sm)
+                                      : launch_k<-1, false, false, 11>(a, s, sms, per_sm);
+    return a.k == 5 ? launch_k<5, false, false, 8>(a, s, sms, per_sm) : launch_k<-1, false, false, 8>(a, s, sms, per_sm);
+  }
   if (a.public_image) {
     if (a.images || a.k < 0) return cudaErrorInvalidValue;
     return a.k == 5 ? launch_k<5, false, true>(a, s, sms, per_sm) : launch_k<-1, false, true>(a, s, sms, per_sm);

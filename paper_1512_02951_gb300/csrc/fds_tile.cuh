@@ -290,6 +290,41 @@ __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_
   }
 }
 
+// ---- packed storage (Sect. 6.4.3): a full tile's 192 channel-blocks are a multiple of 8,
+// so its part of either bit stream starts on a byte boundary
+constexpr int kDcBits = 11;
+
+// bytes of a tile's packed public / private part and their offsets in the image's streams
+// (a full tile: 24 (63 - k) W and 24 (11 + k W) bytes)
+template <int W>
+__device__ __forceinline__ void packed_extent(const TileSlot* sl, bool priv, uint64_t& off, int& bytes) {
+  const int k = sl->k;
+  const int per_cb = priv ? kDcBits + k * W : (63 - k) * W;   // bits per channel-block
+  off = (uint64_t)sl->local * 24ull * (uint64_t)per_cb;
+  bytes = (3 * sl->nb * per_cb + 7) >> 3;
+}
+
+// AES-128-CTR over the tile's packed private part (words at w, stream bytes [off, off +
+// bytes), off a multiple of 4): one thread per keystream block the part overlaps; a block
+// that straddles two tiles is generated by both, each XORing its own words
+__device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int bytes, const TileSlot* sl,
+                                                const uint32_t* rk, const uint32_t* Ts) {
+  const uint64_t b0 = off >> 4;
+  const int nblk = (int)(((off + (uint64_t)bytes + 15) >> 4) - b0);
+  const int nw = (bytes + 3) >> 2;
+  const int skew = (int)((off & 15) >> 2);
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+    uint32_t s[4];
+    ctr_block(sl->iv_hi, sl->iv_lo, b0 + i, s);
+    aes128_encrypt(s, rk, Ts);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int wi = 4 * i + m - skew;
+      if (wi >= 0 && wi < nw) w[wi] ^= s[m];
+    }
+  }
+}
+
 // Exact integer coordinates of 8 F[u][v] (pos = 8u+v) of channel c of tile block b:
 // n[j] = sum over the 64 pixels of pixel * K_j, with the signed-byte weights K_j of
 // table[pos][j][16 words] (word w covers pixels x = 4(w&1) .. +3 of row w>>1).

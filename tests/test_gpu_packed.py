@@ -55,7 +55,7 @@ def test_packed_high_contrast_and_512(api, form):
 
 
 @pytest.mark.parametrize("form", [11, 8])
-@pytest.mark.parametrize("offset", [1, 2, 3])
+@pytest.mark.parametrize("offset", [1, 2, 3, 4, 8])
 def test_packed_public_at_any_alignment(api, form, offset):
     # the packed public fragment may start at any byte; the result is the same bytes
     w, h, k = 136, 72, 5
