@@ -158,11 +158,13 @@ __global__ void __launch_bounds__(32) stats_finish_kernel(const uint8_t* __restr
 cudaError_t launch_image_stats(const uint8_t* img, int width, int height, unsigned long long* hist, long long* sums,
                                cudaStream_t s, int sms) {
   const long long items = (long long)height * ((width + kChunkPx - 1) / kChunkPx);
-  static int per_sm = 0;                         // resident CTAs per SM: one full wave
-  if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, image_stats_kernel, kStatThreads, 0);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  }
+  static const int per_sm = [] {                 // resident CTAs per SM: one full wave
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, image_stats_kernel, kStatThreads, 0) != cudaSuccess ||
+        n < 1)
+      n = 1;
+    return n;
+  }();
   const long long cap = (long long)per_sm * sms;
   const int grid = (int)(items < cap ? items : cap);
   if (grid <= 0) return cudaSuccess;
