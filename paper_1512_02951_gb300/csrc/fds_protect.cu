@@ -17,6 +17,13 @@
 // One staging area (so that three CTAs fit on an SM): the previous tile's bulk stores must
 // have read it before the transform writes it again.
 //
+// Near ties of the int16 forms are not decided inside the tile loop (one exact decision there
+// held every thread of the CTA at a barrier): each is recorded (tile, channel-block,
+// position, the float32-rounded value that was stored) and, once the CTA's tiles have all
+// left, decided exactly from the image in global memory; a changed value is patched into the
+// fragment by XOR with (old ^ new), which is right for the public int16 and, CTR being a
+// stream cipher, for the private ciphertext alike.  The packed forms keep the per-tile queue.
+//
 // Packed storage (Sect. 6.4.3, Table 5; PACK = 11 or 8 bits per AC field): after step 2 the
 // staging area is packed in place into the tile's part of the two bit streams (DC unsigned in
 // 11 bits, AC sign-magnitude in PACK bits, least significant bit first, channel-blocks in
@@ -32,7 +39,7 @@ constexpr int kSmemPix = 0;                                  // 2 pixel tiles
 constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 1 staging area
 constexpr int kSmemT = kSmemStage + kCoefBytes;              // AES tables, 4 KB
 constexpr int kSmemQueue = kSmemT + 4096;                    // near-tie queue
-constexpr int kSmemSlot = kSmemQueue + 4 * kQueueCap;        // 3 tile slots (ring)
+constexpr int kSmemSlot = kSmemQueue + 8 * kQueueCap;        // 3 tile slots (ring)
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
 constexpr int kSmemBytes = kSmemMisc + 32;
@@ -200,6 +207,49 @@ __device__ __forceinline__ void store_private_packed(const TileSlot* sl, const u
   if (t < (bytes & 3)) dst[(bytes & ~3) + t] = src[(bytes & ~3) + t];
 }
 
+// A recorded near tie: x = the tile, y = channel-block | position << 8 | stored int16 << 16.
+// Decide it exactly from the image and patch the fragment in global memory if it changes.
+template <bool BATCH>
+__device__ __forceinline__ void resolve_deferred(const TileArgs& a, uint2 e, int* esc, bool* fail) {
+  const int g = (int)e.x;
+  const int cb = (int)(e.y & 255u), pos = (int)((e.y >> 8) & 63u);
+  const int q0 = (int)(int16_t)(uint16_t)(e.y >> 16);
+  int width, k, local;
+  const uint8_t* px;
+  uint8_t* pub;
+  uint8_t* priv;
+  if (!BATCH) {
+    width = a.width, k = a.k, local = g;
+    px = a.pixels_in;
+    pub = reinterpret_cast<uint8_t*>(a.pub_out);
+    priv = a.priv_out;
+  } else {
+    int lo = 0, hi = a.n_images;                 // tile_start[lo] <= g < tile_start[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(a.tile_start + mid) <= g)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const BatchImage& im = a.images[lo];
+    width = im.width, k = im.k, local = g - __ldg(a.tile_start + lo);
+    px = a.pixels_in + im.pixel_offset;
+    pub = reinterpret_cast<uint8_t*>(a.pub_out) + im.public_offset;
+    priv = a.priv_out + im.private_offset;
+  }
+  const int b = cb / 3, c = cb - 3 * b;
+  int n[9];
+  coords_fwd_global(px + block_offset(width, local * kTileBlocks + b), 3ull * (uint64_t)width, c, pos, a.cfwd, n);
+  const int q = exact_round(n, esc, fail);
+  if (q == q0) return;
+  const int z = zigzag_of(pos >> 3, pos & 7);
+  const uint64_t cbg = (uint64_t)local * kTileCb + (uint64_t)cb;    // channel-block of the image
+  uint16_t* p = z <= k ? reinterpret_cast<uint16_t*>(priv) + cbg * (uint64_t)(k + 1) + z
+                       : reinterpret_cast<uint16_t*>(pub) + cbg * (uint64_t)(63 - k) + (z - k - 1);
+  *p ^= (uint16_t)(q0 ^ q);
+}
+
 // cp.async the pixels of slot sl into pixel tile pix (all threads)
 __device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
   const uint64_t w3 = (uint64_t)sl->width * 3ull;
@@ -225,8 +275,10 @@ __host__ __device__ constexpr int pair_col(int j, int l) {
 template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  constexpr bool DEFER = PACK == 0 && !DEBUG;   // near ties decided after the tile loop
   uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
+  uint2* deferred = reinterpret_cast<uint2*>(smem + kSmemQueue);
   // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
   const int t = threadIdx.x;
@@ -255,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     const TileSlot* sl = slot(s_cur);
     if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot(s_nxt));
     cp_async_wait_all();
-    if (t == 0) misc[0] = 0;
+    if (!DEFER && t == 0) misc[0] = 0;
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
     if constexpr (PACK != 0) {
@@ -378,8 +430,14 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
           mask &= mask - 1;
           const int idx = atomicAdd(&misc[0], 1);
           if (idx < kQueueCap) {
-            queue[idx] = ((uint32_t)cb << 8) | (uint32_t)pos;
-          } else {  // queue full: decide here
+            if constexpr (DEFER) {
+              const int z = zigzag_of(pos >> 3, pos & 7);
+              const uint32_t q0 = (uint16_t)(z <= k ? priv_cb[z] : pub_cb[z - k - 1]);
+              deferred[idx] = make_uint2((uint32_t)cur, (uint32_t)cb | ((uint32_t)pos << 8) | (q0 << 16));
+            } else {
+              queue[idx] = ((uint32_t)cb << 8) | (uint32_t)pos;
+            }
+          } else {  // list full: decide here
             int n[9], esc = 0;
             bool fail = false;
             coords_fwd(tile_px, b, c, pos, a.cfwd, n);
@@ -399,8 +457,8 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
       __syncthreads();   // publishes the schedule entry written after barrier A
       continue;
     }
-    __syncthreads();                                                       // B
-    {
+    if constexpr (!DEFER) {
+      __syncthreads();                                                     // B
       const int nq = min(misc[0], kQueueCap);
       int esc = 0;
       bool fail = false;
@@ -451,6 +509,20 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
   if (t == 0) {
     if (PACK == 0 && have_prev) store_private(slot((it + 2) % 3), smem + kSmemStage);
     bulk_wait_all();
+    if (DEFER) asm volatile("fence.proxy.async.global;\n" ::: "memory");   // bulk writes, then patches
+  }
+  if constexpr (DEFER) {
+    __syncthreads();                                   // every fragment of the CTA is in memory
+    const int nd = min(misc[0], kQueueCap);
+    int esc = 0;
+    bool fail = false;
+    for (int i = t; i < nd; i += kThreads) resolve_deferred<BATCH>(a, deferred[i], &esc, &fail);
+    if (esc) atomicAdd(&misc[2], esc);
+    if (fail) atomicAdd(&misc[3], 1);
+    __syncthreads();
+    if (t == 0) misc[1] += misc[0];
+  }
+  if (t == 0) {
     if (a.counters) {
       if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
       if (misc[2]) atomicAdd(&a.counters[1], (unsigned long long)misc[2]);

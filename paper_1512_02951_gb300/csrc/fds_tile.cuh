@@ -329,18 +329,10 @@ __device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int b
 // n[j] = sum over the 64 pixels of pixel * K_j, with the signed-byte weights K_j of
 // table[pos][j][16 words] (word w covers pixels x = 4(w&1) .. +3 of row w>>1).
 // ROWB: bytes per pixel row of the tile
-template <int ROWB = kRowBytes>
-__device__ __forceinline__ void coords_fwd(const uint8_t* tile, int b, int c, int pos,
-                                           const uint32_t* table, int (&n)[9]) {
-  uint32_t P[16];
-#pragma unroll
-  for (int y = 0; y < 8; ++y) {
-    uint32_t w[6];
-    load_row_shifted<ROWB>(tile, y, b, c, w);
-    // bytes 0, 3, 6, 9 and 12, 15, 18, 21 of w
-    P[2 * y] = __byte_perm(__byte_perm(w[0], w[1], 0x0630u), w[2], 0x5210u);
-    P[2 * y + 1] = __byte_perm(__byte_perm(w[3], w[4], 0x0630u), w[5], 0x5210u);
-  }
+// the dot products of coords_fwd: P[16] = the 64 pixels of the channel-block as bytes (word
+// w covers pixels x = 4(w&1) .. +3 of row w>>1)
+__device__ __forceinline__ void coords_from_pixels(const uint32_t (&P)[16], int pos, const uint32_t* table,
+                                                   int (&n)[9]) {
   const uint4* t4 = reinterpret_cast<const uint4*>(table + pos * 128);
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -356,6 +348,47 @@ __device__ __forceinline__ void coords_fwd(const uint8_t* tile, int b, int c, in
     n[j] = acc;
   }
   n[8] = 0;
+}
+
+// bytes 0, 3, 6, 9 and 12, 15, 18, 21 of a row's six words (channel c already shifted to byte 0)
+__device__ __forceinline__ void row_pixels(const uint32_t (&w)[6], uint32_t& lo, uint32_t& hi) {
+  lo = __byte_perm(__byte_perm(w[0], w[1], 0x0630u), w[2], 0x5210u);
+  hi = __byte_perm(__byte_perm(w[3], w[4], 0x0630u), w[5], 0x5210u);
+}
+
+// Exact integer coordinates of 8 F[u][v] (pos = 8u+v) of channel c of tile block b:
+// n[j] = sum over the 64 pixels of pixel * K_j, with the signed-byte weights K_j of
+// table[pos][j][16 words] (word w covers pixels x = 4(w&1) .. +3 of row w>>1).
+// ROWB: bytes per pixel row of the tile
+template <int ROWB = kRowBytes>
+__device__ __forceinline__ void coords_fwd(const uint8_t* tile, int b, int c, int pos,
+                                           const uint32_t* table, int (&n)[9]) {
+  uint32_t P[16];
+#pragma unroll
+  for (int y = 0; y < 8; ++y) {
+    uint32_t w[6];
+    load_row_shifted<ROWB>(tile, y, b, c, w);
+    row_pixels(w, P[2 * y], P[2 * y + 1]);
+  }
+  coords_from_pixels(P, pos, table, n);
+}
+
+// the same from the image in global memory: blk = the block's top-left pixel (8-byte
+// aligned), row = bytes per image row
+__device__ __forceinline__ void coords_fwd_global(const uint8_t* blk, uint64_t row, int c, int pos,
+                                                  const uint32_t* table, int (&n)[9]) {
+  uint32_t P[16];
+#pragma unroll
+  for (int y = 0; y < 8; ++y) {
+    const uint2* rp = reinterpret_cast<const uint2*>(blk + y * row);
+    const uint2 w01 = __ldg(rp), w23 = __ldg(rp + 1), w45 = __ldg(rp + 2);
+    const uint32_t r[7] = {w01.x, w01.y, w23.x, w23.y, w45.x, w45.y, 0u};
+    uint32_t w[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) w[i] = __funnelshift_r(r[i], r[i + 1], 8 * c);
+    row_pixels(w, P[2 * y], P[2 * y + 1]);
+  }
+  coords_from_pixels(P, pos, table, n);
 }
 
 // Exact integer coordinates of 8 p[y][x] (pos = 8y+x) from int16 coefficients in zigzag
