@@ -209,8 +209,14 @@ __device__ __forceinline__ void store_private_packed(const TileSlot* sl, const u
 
 // A recorded near tie: x = the tile, y = channel-block | position << 8 | stored int16 << 16.
 // Decide it exactly from the image and patch the fragment in global memory if it changes.
-template <bool BATCH>
-__device__ __forceinline__ void resolve_deferred(const TileArgs& a, uint2 e, int* esc, bool* fail) {
+// a patch of the packed streams: XOR bytes p[0], p[1], p[2] with bytes 0, 1, 2 of v
+struct BitPatch {
+  uint8_t* p;
+  uint32_t v;
+};
+
+template <bool BATCH, int PACK>
+__device__ __forceinline__ void resolve_deferred(const TileArgs& a, uint2 e, int* esc, bool* fail, BitPatch* bp) {
   const int g = (int)e.x;
   const int cb = (int)(e.y & 255u), pos = (int)((e.y >> 8) & 63u);
   const int q0 = (int)(int16_t)(uint16_t)(e.y >> 16);
@@ -242,12 +248,19 @@ __device__ __forceinline__ void resolve_deferred(const TileArgs& a, uint2 e, int
   int n[9];
   coords_fwd_global(px + block_offset(width, local * kTileBlocks + b), 3ull * (uint64_t)width, c, pos, a.cfwd, n);
   const int q = exact_round(n, esc, fail);
-  if (q == q0) return;
   const int z = zigzag_of(pos >> 3, pos & 7);
   const uint64_t cbg = (uint64_t)local * kTileCb + (uint64_t)cb;    // channel-block of the image
-  uint16_t* p = z <= k ? reinterpret_cast<uint16_t*>(priv) + cbg * (uint64_t)(k + 1) + z
-                       : reinterpret_cast<uint16_t*>(pub) + cbg * (uint64_t)(63 - k) + (z - k - 1);
-  *p ^= (uint16_t)(q0 ^ q);
+  if constexpr (PACK == 0) {
+    if (q == q0) return;
+    uint16_t* p = z <= k ? reinterpret_cast<uint16_t*>(priv) + cbg * (uint64_t)(k + 1) + z
+                         : reinterpret_cast<uint16_t*>(pub) + cbg * (uint64_t)(63 - k) + (z - k - 1);
+    *p ^= (uint16_t)(q0 ^ q);
+  } else {   // an AC field of PACK bits (a near tie is never the DC coefficient)
+    const uint64_t bit = z <= k ? cbg * (uint64_t)(kDcBits + k * PACK) + kDcBits + (uint64_t)(z - 1) * PACK
+                                : (cbg * (uint64_t)(63 - k) + (uint64_t)(z - k - 1)) * PACK;
+    bp->p = (z <= k ? priv : pub) + (bit >> 3);   // written for every entry: v = 0, nothing to do
+    bp->v = (ac_code<PACK>(q0) ^ ac_code<PACK>(q)) << (bit & 7);
+  }
 }
 
 // cp.async the pixels of slot sl into pixel tile pix (all threads)
@@ -275,7 +288,7 @@ __host__ __device__ constexpr int pair_col(int j, int l) {
 template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr bool DEFER = PACK == 0 && !DEBUG;   // near ties decided after the tile loop
+  constexpr bool DEFER = !DEBUG;   // near ties decided after the tile loop
   uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
   uint2* deferred = reinterpret_cast<uint2*>(smem + kSmemQueue);
@@ -516,7 +529,18 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     const int nd = min(misc[0], kQueueCap);
     int esc = 0;
     bool fail = false;
-    for (int i = t; i < nd; i += kThreads) resolve_deferred<BATCH>(a, deferred[i], &esc, &fail);
+    // packed-stream patches are applied by one thread (fields share bytes; the pixel tiles are
+    // free now and hold them); patches never cross into another tile's bytes or CTA
+    BitPatch* bp = reinterpret_cast<BitPatch*>(smem + kSmemPix);
+    for (int i = t; i < nd; i += kThreads) resolve_deferred<BATCH, PACK>(a, deferred[i], &esc, &fail, bp + i);
+    if constexpr (PACK != 0) {
+      __syncthreads();
+      if (t == 0)
+        for (int i = 0; i < nd; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            if ((bp[i].v >> (8 * j)) & 0xffu) bp[i].p[j] ^= (uint8_t)(bp[i].v >> (8 * j));
+    }
     if (esc) atomicAdd(&misc[2], esc);
     if (fail) atomicAdd(&misc[3], 1);
     __syncthreads();
