@@ -22,7 +22,9 @@
 // position, the float32-rounded value that was stored) and, once the CTA's tiles have all
 // left, decided exactly from the image in global memory; a changed value is patched into the
 // fragment by XOR with (old ^ new), which is right for the public int16 and, CTR being a
-// stream cipher, for the private ciphertext alike.  The packed forms keep the per-tile queue.
+// stream cipher, for the private ciphertext alike.  The packed forms patch the field's code
+// difference into the bit streams (one thread per CTA: fields share bytes).  The per-tile
+// queue remains for the debug export only.
 //
 // Packed storage (Sect. 6.4.3, Table 5; PACK = 11 or 8 bits per AC field): after step 2 the
 // staging area is packed in place into the tile's part of the two bit streams (DC unsigned in
