@@ -10,23 +10,22 @@
 //      rounding on pairs of columns with packed f32x2 instructions, bit-identical per lane);
 //      every coefficient rounded to int16 and written to the public or private staging area
 //      at its zigzag position; coefficients within the float32 error guard of a half-integer
-//      are queued
-//   B. 2. queued coefficients are re-decided exactly (integer coordinates in Z[cos(pi/16)])
-//   C. 3. the public fragment leaves (bulk store) while AES-128-CTR encrypts the private
+//      are recorded (below)
+//   C. 2. the public fragment leaves (bulk store) while AES-128-CTR encrypts the private
 //      staging area, one thread per 16-byte keystream block
 // One staging area (so that three CTAs fit on an SM): the previous tile's bulk stores must
 // have read it before the transform writes it again.
 //
-// Near ties of the int16 forms are not decided inside the tile loop (one exact decision there
-// held every thread of the CTA at a barrier): each is recorded (tile, channel-block,
-// position, the float32-rounded value that was stored) and, once the CTA's tiles have all
-// left, decided exactly from the image in global memory; a changed value is patched into the
-// fragment by XOR with (old ^ new), which is right for the public int16 and, CTR being a
-// stream cipher, for the private ciphertext alike.  The packed forms patch the field's code
-// difference into the bit streams (one thread per CTA: fields share bytes).  The per-tile
-// queue remains for the debug export only.
+// Near ties are not decided inside the tile loop (one exact decision there held every thread
+// of the CTA at a barrier): each is recorded (tile, channel-block, position, the
+// float32-rounded value that was stored) and, once the CTA's tiles have all left, decided
+// exactly (integer coordinates in Z[cos(pi/16)]) from the image in global memory; a changed
+// value is patched into the fragment by XOR with (old ^ new), which is right for the public
+// int16 and, CTR being a stream cipher, for the private ciphertext alike.  The packed forms
+// patch the field's code difference into the bit streams (one thread per CTA: fields share
+// bytes).  A full list means the value is decided in place, from the tile in shared memory.
 //
-// Packed storage (Sect. 6.4.3, Table 5; PACK = 11 or 8 bits per AC field): after step 2 the
+// Packed storage (Sect. 6.4.3, Table 5; PACK = 11 or 8 bits per AC field): after step 1 the
 // staging area is packed in place into the tile's part of the two bit streams (DC unsigned in
 // 11 bits, AC sign-magnitude in PACK bits, least significant bit first, channel-blocks in
 // stream order), and AES-128-CTR runs over the packed private bytes at their offset in the
@@ -290,10 +289,8 @@ __host__ __device__ constexpr int pair_col(int j, int l) {
 template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr bool DEFER = !DEBUG;   // near ties decided after the tile loop
   uint32_t* Ts = reinterpret_cast<uint32_t*>(smem + kSmemT);
-  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
-  uint2* deferred = reinterpret_cast<uint2*>(smem + kSmemQueue);
+  uint2* deferred = reinterpret_cast<uint2*>(smem + kSmemQueue);   // near ties, after the tile loop
   // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
   const int t = threadIdx.x;
@@ -322,7 +319,6 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     const TileSlot* sl = slot(s_cur);
     if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot(s_nxt));
     cp_async_wait_all();
-    if (!DEFER && t == 0) misc[0] = 0;
     __syncthreads();                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
     if constexpr (PACK != 0) {
@@ -445,13 +441,9 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
           mask &= mask - 1;
           const int idx = atomicAdd(&misc[0], 1);
           if (idx < kQueueCap) {
-            if constexpr (DEFER) {
-              const int z = zigzag_of(pos >> 3, pos & 7);
-              const uint32_t q0 = (uint16_t)(z <= k ? priv_cb[z] : pub_cb[z - k - 1]);
-              deferred[idx] = make_uint2((uint32_t)cur, (uint32_t)cb | ((uint32_t)pos << 8) | (q0 << 16));
-            } else {
-              queue[idx] = ((uint32_t)cb << 8) | (uint32_t)pos;
-            }
+            const int z = zigzag_of(pos >> 3, pos & 7);
+            const uint32_t q0 = (uint16_t)(z <= k ? priv_cb[z] : pub_cb[z - k - 1]);
+            deferred[idx] = make_uint2((uint32_t)cur, (uint32_t)cb | ((uint32_t)pos << 8) | (q0 << 16));
           } else {  // list full: decide here
             int n[9], esc = 0;
             bool fail = false;
@@ -471,28 +463,6 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
     if (DEBUG) {
       __syncthreads();   // publishes the schedule entry written after barrier A
       continue;
-    }
-    if constexpr (!DEFER) {
-      __syncthreads();                                                     // B
-      const int nq = min(misc[0], kQueueCap);
-      int esc = 0;
-      bool fail = false;
-      for (int i = t; i < nq; i += kThreads) {
-        const uint32_t e = queue[i];
-        const int ecb = (int)(e >> 8), pos = (int)(e & 255);
-        const int eb = ecb / 3, ec = ecb - 3 * eb;
-        int n[9];
-        coords_fwd(tile_px, eb, ec, pos, a.cfwd, n);
-        const int q = exact_round(n, &esc, &fail);
-        const int z = zigzag_of(pos >> 3, pos & 7);
-        if (z <= k)
-          privst[ecb * (k + 1) + z] = (int16_t)q;
-        else
-          pubst[ecb * npub + z - k - 1] = (int16_t)q;
-      }
-      if (esc) atomicAdd(&misc[2], esc);
-      if (fail) atomicAdd(&misc[3], 1);
-      if (t == 0) misc[1] += misc[0];
     }
     if constexpr (PACK != 0) {
       __syncthreads();                                 // every staged coefficient is final
@@ -524,9 +494,9 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
   if (t == 0) {
     if (PACK == 0 && have_prev) store_private(slot((it + 2) % 3), smem + kSmemStage);
     bulk_wait_all();
-    if (DEFER) asm volatile("fence.proxy.async.global;\n" ::: "memory");   // bulk writes, then patches
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");   // bulk writes, then the patches
   }
-  if constexpr (DEFER) {
+  {
     __syncthreads();                                   // every fragment of the CTA is in memory
     const int nd = min(misc[0], kQueueCap);
     int esc = 0;
