@@ -13,12 +13,12 @@
 //      are recorded (below)
 //   C. 2. the public fragment leaves (bulk store) while AES-128-CTR encrypts the private
 //      staging area, one thread per 16-byte keystream block
-// One staging area (so that three CTAs fit on an SM): the previous tile's bulk stores must
-// have read it before the transform writes it again.
+// One staging area (so that four CTAs, 80 registers a thread, fit on an SM): the previous
+// tile's bulk stores must have read it before the transform writes it again.
 //
 // Near ties are not decided inside the tile loop (one exact decision there held every thread
 // of the CTA at a barrier): each is recorded (tile, channel-block, position, the
-// float32-rounded value that was stored) and, once the CTA's tiles have all left, decided
+// float32-rounded value that was stored; 192 per CTA) and, once the CTA's tiles have all left, decided
 // exactly (integer coordinates in Z[cos(pi/16)]) from the image in global memory; a changed
 // value is patched into the fragment by XOR with (old ^ new), which is right for the public
 // int16 and, CTR being a stream cipher, for the private ciphertext alike.  The packed forms
@@ -35,12 +35,13 @@
 
 namespace fds {
 
-constexpr int kPCtasPerSm = 3;
+constexpr int kPCtasPerSm = 4;
 constexpr int kSmemPix = 0;                                  // 2 pixel tiles
 constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 1 staging area
 constexpr int kSmemT = kSmemStage + kCoefBytes;              // AES tables, 4 KB
 constexpr int kSmemQueue = kSmemT + 4096;                    // near-tie queue
-constexpr int kSmemSlot = kSmemQueue + 8 * kQueueCap;        // 3 tile slots (ring)
+constexpr int kDeferCap = 192;                               // recorded near ties per CTA
+constexpr int kSmemSlot = kSmemQueue + 8 * kDeferCap;        // 3 tile slots (ring)
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
 constexpr int kSmemBytes = kSmemMisc + 32;
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
           const int pos = __ffsll((long long)mask) - 1;
           mask &= mask - 1;
           const int idx = atomicAdd(&misc[0], 1);
-          if (idx < kQueueCap) {
+          if (idx < kDeferCap) {
             const int z = zigzag_of(pos >> 3, pos & 7);
             const uint32_t q0 = (uint16_t)(z <= k ? priv_cb[z] : pub_cb[z - k - 1]);
             deferred[idx] = make_uint2((uint32_t)cur, (uint32_t)cb | ((uint32_t)pos << 8) | (q0 << 16));
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
   }
   {
     __syncthreads();                                   // every fragment of the CTA is in memory
-    const int nd = min(misc[0], kQueueCap);
+    const int nd = min(misc[0], kDeferCap);
     int esc = 0;
     bool fail = false;
     // packed-stream patches are applied by one thread (fields share bytes; the pixel tiles are
