@@ -273,7 +273,10 @@ int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8
  * fds_restore_image_host: restores dev_public / dev_private into dev_pixels and copies the
  * pixels to host_pixels.  Kernels run on `stream`: earlier work on it comes
  * first (the copy streams wait for it), and when it completes every copy of the call has
- * completed.  strips: 1..64.
+ * completed.  Each caller stream has its own copy streams (up to 16 caller streams per
+ * device; further ones share one pair), so calls on different streams, for example two
+ * images in flight on two streams with their own buffers, overlap their copies.
+ * strips: 1..64.
  * Device alignments as fds_protect_image; host buffers should be pinned (pageable memory
  * works but does not overlap). */
 int fds_protect_image_host(const uint8_t* host_pixels, uint8_t* dev_pixels, int32_t width,

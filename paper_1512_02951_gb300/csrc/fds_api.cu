@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -622,11 +623,21 @@ namespace {
 struct HostLanes {
   cudaStream_t in = nullptr, out = nullptr;   // host -> device and device -> host copies
 };
-HostLanes g_lanes[kMaxDevices];
+// One pair of copy streams per device and caller stream, so that calls on one stream keep
+// their copies in order while calls on different streams overlap theirs.  Beyond
+// kLaneStreams caller streams on a device, further streams share one pair.
+constexpr size_t kLaneStreams = 16;
+std::map<std::pair<int, cudaStream_t>, HostLanes> g_lanes;   // guarded by g_mu
+size_t g_lane_count[kMaxDevices];
 
-int host_lanes(int dev, HostLanes** lanes) {
+int host_lanes(int dev, cudaStream_t caller, HostLanes** lanes) {
   std::lock_guard<std::mutex> lk(g_mu);
-  HostLanes& l = g_lanes[dev];
+  auto key = std::make_pair(dev, caller);
+  if (!g_lanes.count(key)) {
+    if (g_lane_count[dev] >= kLaneStreams) key.second = nullptr;
+    if (!g_lanes.count(key)) ++g_lane_count[dev];
+  }
+  HostLanes& l = g_lanes[key];
   cudaError_t e = cudaSuccess;
   if (!l.in && (e = cudaStreamCreateWithFlags(&l.in, cudaStreamNonBlocking)) != cudaSuccess)
     return cuda_fail(e, "copy stream");
@@ -695,8 +706,8 @@ int fds_protect_image_host(const uint8_t* host_pixels, uint8_t* dev_pixels, int3
   int dev = 0;
   if ((rc = ensure_init(&dev))) return rc;
   HostLanes* ln = nullptr;
-  if ((rc = host_lanes(dev, &ln))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = host_lanes(dev, s, &ln))) return rc;
   const uint64_t w3 = 3ull * (uint64_t)width, bx = (uint64_t)(width / 8);
   const uint64_t pub_row = bx * 3ull * (uint64_t)(63 - k), priv_row = bx * 3ull * 2ull * (uint64_t)(k + 1);
   uint32_t rk[44];
@@ -752,8 +763,8 @@ int fds_restore_image_host(const int16_t* dev_public, const uint8_t* dev_private
   int dev = 0;
   if ((rc = ensure_init(&dev))) return rc;
   HostLanes* ln = nullptr;
-  if ((rc = host_lanes(dev, &ln))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = host_lanes(dev, s, &ln))) return rc;
   const uint64_t w3 = 3ull * (uint64_t)width, bx = (uint64_t)(width / 8);
   const uint64_t pub_row = bx * 3ull * (uint64_t)(63 - k), priv_row = bx * 3ull * 2ull * (uint64_t)(k + 1);
   uint32_t rk[44];

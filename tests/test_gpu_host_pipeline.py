@@ -67,3 +67,39 @@ def test_against_the_oracle_and_pageable_memory(api):
 
 def test_full_size(api):
     _run(api, synth.make_image(4096, 4096, 2), 5, 8)
+
+
+def test_two_streams_in_flight(api):
+    # images alternating over two streams, each with its own buffers and its own copy streams:
+    # every call's copies still end before its stream goes on, whatever runs on the other
+    h, w, k = 512, 384, 5
+    pub_b, priv_b = api.sizes(w, h, k)
+    imgs = [synth.make_image(w, h, 40 + i) for i in range(6)]
+    keys = [(synth.make_key(50 + i), synth.make_iv(60 + i)) for i in range(6)]
+    lanes = []
+    for _ in range(2):
+        lanes.append(dict(
+            s=torch.cuda.Stream(DEV), px=torch.empty((h, w, 3), dtype=torch.uint8, device=DEV),
+            pub=torch.empty(pub_b // 2, dtype=torch.int16, device=DEV),
+            priv=torch.empty(priv_b, dtype=torch.uint8, device=DEV),
+            out=torch.empty((h, w, 3), dtype=torch.uint8, device=DEV)))
+    host_in = [torch.from_numpy(m).pin_memory() for m in imgs]
+    host_pub = [torch.empty(pub_b // 2, dtype=torch.int16).pin_memory() for _ in imgs]
+    host_priv = [torch.empty(priv_b, dtype=torch.uint8).pin_memory() for _ in imgs]
+    host_out = [torch.empty((h, w, 3), dtype=torch.uint8).pin_memory() for _ in imgs]
+    torch.cuda.synchronize()
+    for i in range(len(imgs)):
+        ln = lanes[i % 2]
+        key, iv = keys[i]
+        with torch.cuda.stream(ln["s"]):
+            api.protect_image_host(host_in[i], ln["px"], key, iv, k, ln["pub"], ln["priv"],
+                                   host_pub[i], host_priv[i], 2)
+            api.restore_image_host(ln["pub"], ln["priv"], ln["out"], host_out[i], key, iv, k, 2)
+    torch.cuda.synchronize()
+    for i, img in enumerate(imgs):
+        key, iv = keys[i]
+        want_pub, want_priv = api.protect_image(torch.from_numpy(img).to(DEV), key, iv, k)
+        want_back = api.restore_image(want_pub, want_priv, w, h, k, key, iv)
+        assert np.array_equal(host_pub[i].numpy(), want_pub.reshape(-1).cpu().numpy()), i
+        assert host_priv[i].numpy().tobytes() == want_priv.cpu().numpy().tobytes(), i
+        assert np.array_equal(host_out[i].numpy(), want_back.cpu().numpy()), i
