@@ -300,7 +300,7 @@ int fds_restore_image_host(const int16_t* dev_public, const uint8_t* dev_private
 int fds_public_image(const int16_t* public_in, int32_t width, int32_t height, int32_t k,
                      uint8_t* image_out, void* stream);
 
-/* Statistics used to judge protected images (Sect. 6.6): the per-channel histogram (6.6.1) and
+/* Statistics used to assess protected images (Sect. 6.6): the per-channel histogram (6.6.1) and
  * exact integer sums for the correlation coefficient of adjacent pixels (6.6.2), over every
  * pair of a pixel and its right, lower and lower-right neighbour:
  *   r = (n Sxy - Sx Sy) / sqrt((n Sxx - Sx^2)(n Syy - Sy^2)).

@@ -1,4 +1,4 @@
-"""The paper's own form of the public fragment and the statistics used to judge it.
+"""The paper's own form of the public fragment and the statistics used to assess it.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
