@@ -248,6 +248,45 @@ def test_4096_full_size_sampled(api, k):
     assert 0.88 < frac < 0.97
 
 
+@pytest.mark.parametrize("k", [5, 63])
+def test_beyond_4gib_sampled(api, k):
+    # 40960 x 36864 RGB: 4.53 GB of pixels, so pixel offsets pass 2^32; k = 5 makes an 8.2 GB
+    # public fragment, k = 63 a 9.1 GB private one (byte offsets and keystream positions past
+    # 2^32).  Content: a 1024^2 generator image tiled, XORed with random low bits per pixel.
+    w, h = 40960, 36864
+    bx = w // 8
+    key, iv = synth.make_key(4000 + k), synth.make_iv(5000 + k)
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(17 + k)
+    img = torch.from_numpy(synth.make_image(1024, 1024, 7)).to(DEV).repeat(h // 1024, w // 1024, 1)
+    img ^= torch.randint(0, 4, img.shape, dtype=torch.uint8, device=DEV, generator=gen)
+    pub, priv = api.protect_image(img, key, iv, k)
+    back = api.restore_image(pub, priv, w, h, k, key, iv)
+    torch.cuda.synchronize()
+    pub_row, priv_row, px_row = bx * 3 * 2 * (63 - k), bx * 3 * 2 * (k + 1), 8 * w * 3
+    rows = {(0, 2), (h // 8 - 2, h // 8)}
+    for per_row in (px_row, pub_row, priv_row):      # the block rows around byte 2^32 of each buffer
+        r = (1 << 32) // per_row if per_row else h
+        if r + 2 <= h // 8:
+            rows.add((r - 1, r + 2))
+    assert len(rows) == 4                          # pixels and one fragment pass 2^32
+    for r0, r1 in sorted(rows):
+        strip = img[8 * r0: 8 * r1].cpu().numpy()
+        q, _ = ofds.quantised_dct(odct.image_to_blocks(strip))
+        part1, part2 = ofds.split(q.astype(np.int16), k)
+        off = r0 * priv_row
+        want_ct = oaes.ctr_xcrypt(key, iv, np.ascontiguousarray(part1).astype("<i2").tobytes(), offset=off)
+        if k < 63:
+            assert np.array_equal(pub[r0: r1].cpu().numpy(), part2), (r0, r1)
+        got_ct = priv[off: off + len(want_ct)].cpu().numpy().tobytes()
+        assert got_ct == want_ct, (r0, r1)
+        p = ofds.quantised_idct(ofds.merge(part1.astype(np.int64), part2.astype(np.int64)))
+        want = odct.blocks_to_image(np.clip(p, 0, 255).astype(np.uint8))
+        assert np.array_equal(back[8 * r0: 8 * r1].cpu().numpy(), want), (r0, r1)
+    del img, pub, priv, back
+    torch.cuda.empty_cache()
+
+
 def test_queue_overflow_forward(api):
     # a block with exact ties at several irrational positions, repeated over whole tiles, puts
     # more near-ties into one tile than its queue holds
