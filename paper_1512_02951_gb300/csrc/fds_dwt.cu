@@ -39,7 +39,12 @@ struct DwtArgs {
   uint64_t iv_hi, iv_lo;
   uint32_t kiv[8];             // key and IV as big-endian words (the hashed prefix)
   uint32_t rk[44];
+  // the hashes' working variables after the rounds that read only key || IV: SHA-256 after
+  // rounds 0..7 (message words 0..7), SHA-512 after rounds 0..3 (words 0..3)
+  uint32_t mid256[8];
+  uint64_t mid512[8];
 };
+constexpr int kMid256 = 8, kMid512 = 4;
 
 // one level of lifting on 2m samples v[0], v[s], .., v[(2m-1) s] -> [low | high] in place
 template <int M>
@@ -143,12 +148,12 @@ __device__ __forceinline__ void mask2(const DwtArgs& a, long long b, uint64_t l1
   w[11] = ((uint32_t)(l1 >> 32) & 0xffu) << 24 | 0x00800000u;
   w[12] = w[13] = w[14] = 0u;
   w[15] = 8u * (32u + 8u + 5u);
-  uint32_t h[8];
+  uint32_t v[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) h[i] = c_sha256_h0[i];
-  sha256_compress(h, w);
+  for (int i = 0; i < 8; ++i) v[i] = a.mid256[i];
+  sha256_rounds<kMid256>(v, w);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) m[i] = bswap32(h[i]);
+  for (int i = 0; i < 4; ++i) m[i] = bswap32(c_sha256_h0[i] + v[i]);
 }
 
 // SHA-512(key || IV || block index || 16 bytes of level 2): digest bytes 0..59 as 15 words
@@ -164,13 +169,13 @@ __device__ __forceinline__ void mask3(const DwtArgs& a, long long b, const uint3
 #pragma unroll
   for (int i = 8; i < 15; ++i) w[i] = 0;
   w[15] = 8ull * (32 + 8 + 16);
-  uint64_t h[8];
+  uint64_t v[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) h[i] = c_sha512_h0[i];
-  sha512_compress(h, w);
+  for (int i = 0; i < 8; ++i) v[i] = a.mid512[i];
+  sha512_rounds<kMid512>(v, w);
 #pragma unroll
   for (int i = 0; i < kL3Words; ++i) {
-    const uint64_t x = h[i >> 1];
+    const uint64_t x = c_sha512_h0[i >> 1] + v[i >> 1];
     m[i] = bswap32((i & 1) ? (uint32_t)x : (uint32_t)(x >> 32));
   }
 }
@@ -301,6 +306,45 @@ __global__ void __launch_bounds__(kDwtThreads) dwt_restore_kernel(const __grid_c
   }
 }
 
+// The rounds of SHA-256 and SHA-512 (FIPS 180-4) that read only key || IV, the same for every
+// block of a launch, run once here on the host; the kernels go on from the state they leave.
+struct ShaConsts {
+  uint64_t k[80], h0[8];
+};
+static void hash_midstates(DwtArgs& a) {
+  static const ShaConsts sc = [] {
+    ShaConsts c;
+    sha512_constants(c.k, c.h0);
+    return c;
+  }();
+  auto r32 = [](uint32_t x, int n) { return (x >> n) | (x << (32 - n)); };
+  auto r64 = [](uint64_t x, int n) { return (x >> n) | (x << (64 - n)); };
+  uint32_t v[8];
+  for (int i = 0; i < 8; ++i) v[i] = (uint32_t)(sc.h0[i] >> 32);   // SHA-256's: the top 32 bits
+  for (int t = 0; t < kMid256; ++t) {
+    const uint32_t e = v[4], f = v[5], g = v[6], av = v[0], b = v[1], c = v[2];
+    const uint32_t t1 = v[7] + (r32(e, 6) ^ r32(e, 11) ^ r32(e, 25)) + ((e & f) ^ (~e & g)) +
+                        (uint32_t)(sc.k[t] >> 32) + a.kiv[t];
+    const uint32_t t2 = (r32(av, 2) ^ r32(av, 13) ^ r32(av, 22)) + ((av & b) ^ (av & c) ^ (b & c));
+    for (int i = 7; i > 0; --i) v[i] = v[i - 1];
+    v[4] += t1;
+    v[0] = t1 + t2;
+  }
+  for (int i = 0; i < 8; ++i) a.mid256[i] = v[i];
+  uint64_t u[8];
+  for (int i = 0; i < 8; ++i) u[i] = sc.h0[i];
+  for (int t = 0; t < kMid512; ++t) {
+    const uint64_t e = u[4], f = u[5], g = u[6], av = u[0], b = u[1], c = u[2];
+    const uint64_t wt = ((uint64_t)a.kiv[2 * t] << 32) | a.kiv[2 * t + 1];
+    const uint64_t t1 = u[7] + (r64(e, 14) ^ r64(e, 18) ^ r64(e, 41)) + ((e & f) ^ (~e & g)) + sc.k[t] + wt;
+    const uint64_t t2 = (r64(av, 28) ^ r64(av, 34) ^ r64(av, 39)) + ((av & b) ^ (av & c) ^ (b & c));
+    for (int i = 7; i > 0; --i) u[i] = u[i - 1];
+    u[4] += t1;
+    u[0] = t1 + t2;
+  }
+  for (int i = 0; i < 8; ++i) a.mid512[i] = u[i];
+}
+
 static void dwt_args(DwtArgs& a, int width, int height, const uint8_t key[16], const uint8_t iv[16],
                      const uint32_t rk[44], const uint32_t* T) {
   a.width = width;
@@ -314,6 +358,7 @@ static void dwt_args(DwtArgs& a, int width, int height, const uint8_t key[16], c
   a.iv_hi = ((uint64_t)a.kiv[4] << 32) | a.kiv[5];
   a.iv_lo = ((uint64_t)a.kiv[6] << 32) | a.kiv[7];
   for (int i = 0; i < 44; ++i) a.rk[i] = rk[i];
+  hash_midstates(a);
 }
 
 cudaError_t launch_dwt_protect(const uint8_t* data, int width, int height, const uint8_t key[16],

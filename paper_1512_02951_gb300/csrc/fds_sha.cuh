@@ -19,84 +19,114 @@ static __constant__ uint32_t c_sha256_h0[8];
 __device__ __forceinline__ uint64_t rotr64(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
 __device__ __forceinline__ uint32_t rotr32(uint32_t x, int n) { return __funnelshift_r(x, x, n); }
 
-// one SHA-512 compression of the 16 big-endian words w into state h; the 80 rounds run as
-// five passes of 16 (the schedule ring index is then fixed in each unrolled round, and the
-// code stays small enough for the instruction cache)
-__device__ __forceinline__ void sha512_compress(uint64_t (&h)[8], uint64_t (&w)[16]) {
-  uint64_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
-#pragma unroll 1
-  for (int t0 = 0; t0 < 80; t0 += 16) {
+// SHA-512 rounds R0..79 of one compression on the working variables v = (a, .., h) entering
+// round R0, with the 16 big-endian message words w (all 16 are needed for the schedule).  The
+// rounds run as passes of 16 (the schedule ring index is then fixed in each unrolled round, and
+// the code stays small enough for the instruction cache); rounds R0..15 of the first pass are
+// unrolled.
+template <int R0 = 0>
+__device__ __forceinline__ void sha512_rounds(uint64_t (&v)[8], uint64_t (&w)[16]) {
+  uint64_t a = v[0], b = v[1], c = v[2], d = v[3], e = v[4], f = v[5], g = v[6], hh = v[7];
+  auto round = [&](int t, uint64_t wt) {
+    const uint64_t S1 = rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41);
+    const uint64_t ch = (e & f) ^ (~e & g);
+    const uint64_t t1 = hh + S1 + ch + c_sha512_k[t] + wt;
+    const uint64_t S0 = rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39);
+    const uint64_t maj = (a & b) ^ (a & c) ^ (b & c);
+    const uint64_t t2 = S0 + maj;
+    hh = g;
+    g = f;
+    f = e;
+    e = d + t1;
+    d = c;
+    c = b;
+    b = a;
+    a = t1 + t2;
+  };
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (t0 > 0) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
-        const uint64_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
-        const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
-        const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
-        w[j] += s0 + w[(j + 9) & 15] + s1;
-      }
-      const uint64_t S1 = rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41);
-      const uint64_t ch = (e & f) ^ (~e & g);
-      const uint64_t t1 = hh + S1 + ch + c_sha512_k[t0 + j] + w[j];
-      const uint64_t S0 = rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39);
-      const uint64_t maj = (a & b) ^ (a & c) ^ (b & c);
-      const uint64_t t2 = S0 + maj;
-      hh = g;
-      g = f;
-      f = e;
-      e = d + t1;
-      d = c;
-      c = b;
-      b = a;
-      a = t1 + t2;
+  for (int j = R0; j < 16; ++j) round(j, w[j]);
+#pragma unroll 1
+  for (int t0 = 16; t0 < 80; t0 += 16) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
+      const uint64_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
+      const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
+      const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
+      w[j] += s0 + w[(j + 9) & 15] + s1;
+      round(t0 + j, w[j]);
     }
   }
-  h[0] += a;
-  h[1] += b;
-  h[2] += c;
-  h[3] += d;
-  h[4] += e;
-  h[5] += f;
-  h[6] += g;
-  h[7] += hh;
+  v[0] = a;
+  v[1] = b;
+  v[2] = c;
+  v[3] = d;
+  v[4] = e;
+  v[5] = f;
+  v[6] = g;
+  v[7] = hh;
 }
 
-// one SHA-256 compression of the 16 big-endian words w into state h (four passes of 16)
-__device__ __forceinline__ void sha256_compress(uint32_t (&h)[8], uint32_t (&w)[16]) {
-  uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
+// one SHA-512 compression of the 16 big-endian words w into state h
+__device__ __forceinline__ void sha512_compress(uint64_t (&h)[8], uint64_t (&w)[16]) {
+  uint64_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = h[i];
+  sha512_rounds<0>(v, w);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] += v[i];
+}
+
+// SHA-256 rounds R0..63 on the working variables v entering round R0 (as sha512_rounds)
+template <int R0 = 0>
+__device__ __forceinline__ void sha256_rounds(uint32_t (&v)[8], uint32_t (&w)[16]) {
+  uint32_t a = v[0], b = v[1], c = v[2], d = v[3], e = v[4], f = v[5], g = v[6], hh = v[7];
+  auto round = [&](int t, uint32_t wt) {
+    const uint32_t S1 = rotr32(e, 6) ^ rotr32(e, 11) ^ rotr32(e, 25);
+    const uint32_t ch = (e & f) ^ (~e & g);
+    const uint32_t t1 = hh + S1 + ch + c_sha256_k[t] + wt;
+    const uint32_t S0 = rotr32(a, 2) ^ rotr32(a, 13) ^ rotr32(a, 22);
+    const uint32_t maj = (a & b) ^ (a & c) ^ (b & c);
+    const uint32_t t2 = S0 + maj;
+    hh = g;
+    g = f;
+    f = e;
+    e = d + t1;
+    d = c;
+    c = b;
+    b = a;
+    a = t1 + t2;
+  };
+#pragma unroll
+  for (int j = R0; j < 16; ++j) round(j, w[j]);
 #pragma unroll 1
-  for (int t0 = 0; t0 < 64; t0 += 16) {
+  for (int t0 = 16; t0 < 64; t0 += 16) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      if (t0 > 0) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
-        const uint32_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
-        const uint32_t s0 = rotr32(x15, 7) ^ rotr32(x15, 18) ^ (x15 >> 3);
-        const uint32_t s1 = rotr32(x2, 17) ^ rotr32(x2, 19) ^ (x2 >> 10);
-        w[j] += s0 + w[(j + 9) & 15] + s1;
-      }
-      const uint32_t S1 = rotr32(e, 6) ^ rotr32(e, 11) ^ rotr32(e, 25);
-      const uint32_t ch = (e & f) ^ (~e & g);
-      const uint32_t t1 = hh + S1 + ch + c_sha256_k[t0 + j] + w[j];
-      const uint32_t S0 = rotr32(a, 2) ^ rotr32(a, 13) ^ rotr32(a, 22);
-      const uint32_t maj = (a & b) ^ (a & c) ^ (b & c);
-      const uint32_t t2 = S0 + maj;
-      hh = g;
-      g = f;
-      f = e;
-      e = d + t1;
-      d = c;
-      c = b;
-      b = a;
-      a = t1 + t2;
+      const uint32_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
+      const uint32_t s0 = rotr32(x15, 7) ^ rotr32(x15, 18) ^ (x15 >> 3);
+      const uint32_t s1 = rotr32(x2, 17) ^ rotr32(x2, 19) ^ (x2 >> 10);
+      w[j] += s0 + w[(j + 9) & 15] + s1;
+      round(t0 + j, w[j]);
     }
   }
-  h[0] += a;
-  h[1] += b;
-  h[2] += c;
-  h[3] += d;
-  h[4] += e;
-  h[5] += f;
-  h[6] += g;
-  h[7] += hh;
+  v[0] = a;
+  v[1] = b;
+  v[2] = c;
+  v[3] = d;
+  v[4] = e;
+  v[5] = f;
+  v[6] = g;
+  v[7] = hh;
+}
+
+// one SHA-256 compression of the 16 big-endian words w into state h
+__device__ __forceinline__ void sha256_compress(uint32_t (&h)[8], uint32_t (&w)[16]) {
+  uint32_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = h[i];
+  sha256_rounds<0>(v, w);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] += v[i];
 }
 
 // this translation unit's copy of the constants, to the current device
