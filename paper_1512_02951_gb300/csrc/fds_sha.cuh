@@ -22,8 +22,7 @@ __device__ __forceinline__ uint32_t rotr32(uint32_t x, int n) { return __funnels
 // SHA-512 rounds R0..79 of one compression on the working variables v = (a, .., h) entering
 // round R0, with the 16 big-endian message words w (all 16 are needed for the schedule).  The
 // rounds run as passes of 16 (the schedule ring index is then fixed in each unrolled round, and
-// the code stays small enough for the instruction cache); rounds R0..15 of the first pass are
-// unrolled.
+// the code stays small enough for the instruction cache).
 template <int R0 = 0>
 __device__ __forceinline__ void sha512_rounds(uint64_t (&v)[8], uint64_t (&w)[16]) {
   uint64_t a = v[0], b = v[1], c = v[2], d = v[3], e = v[4], f = v[5], g = v[6], hh = v[7];
@@ -43,16 +42,22 @@ __device__ __forceinline__ void sha512_rounds(uint64_t (&v)[8], uint64_t (&w)[16
     b = a;
     a = t1 + t2;
   };
+  // from round 0 the first pass is the loop's (one copy of the body); from a later round it
+  // is unrolled ahead of the loop
+  if constexpr (R0 > 0) {
 #pragma unroll
-  for (int j = R0; j < 16; ++j) round(j, w[j]);
+    for (int j = R0; j < 16; ++j) round(j, w[j]);
+  }
 #pragma unroll 1
-  for (int t0 = 16; t0 < 80; t0 += 16) {
+  for (int t0 = R0 > 0 ? 16 : 0; t0 < 80; t0 += 16) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
-      const uint64_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
-      const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
-      const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
-      w[j] += s0 + w[(j + 9) & 15] + s1;
+    for (int j = 0; j < 16; ++j) {
+      if (t0 > 0) {   // w[t] = sigma1(w[t-2]) + w[t-7] + sigma0(w[t-15]) + w[t-16], in the ring
+        const uint64_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
+        const uint64_t s0 = rotr64(x15, 1) ^ rotr64(x15, 8) ^ (x15 >> 7);
+        const uint64_t s1 = rotr64(x2, 19) ^ rotr64(x2, 61) ^ (x2 >> 6);
+        w[j] += s0 + w[(j + 9) & 15] + s1;
+      }
       round(t0 + j, w[j]);
     }
   }
@@ -96,16 +101,20 @@ __device__ __forceinline__ void sha256_rounds(uint32_t (&v)[8], uint32_t (&w)[16
     b = a;
     a = t1 + t2;
   };
+  if constexpr (R0 > 0) {
 #pragma unroll
-  for (int j = R0; j < 16; ++j) round(j, w[j]);
+    for (int j = R0; j < 16; ++j) round(j, w[j]);
+  }
 #pragma unroll 1
-  for (int t0 = 16; t0 < 64; t0 += 16) {
+  for (int t0 = R0 > 0 ? 16 : 0; t0 < 64; t0 += 16) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const uint32_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
-      const uint32_t s0 = rotr32(x15, 7) ^ rotr32(x15, 18) ^ (x15 >> 3);
-      const uint32_t s1 = rotr32(x2, 17) ^ rotr32(x2, 19) ^ (x2 >> 10);
-      w[j] += s0 + w[(j + 9) & 15] + s1;
+      if (t0 > 0) {
+        const uint32_t x15 = w[(j + 1) & 15], x2 = w[(j + 14) & 15];
+        const uint32_t s0 = rotr32(x15, 7) ^ rotr32(x15, 18) ^ (x15 >> 3);
+        const uint32_t s1 = rotr32(x2, 17) ^ rotr32(x2, 19) ^ (x2 >> 10);
+        w[j] += s0 + w[(j + 9) & 15] + s1;
+      }
       round(t0 + j, w[j]);
     }
   }
