@@ -103,3 +103,36 @@ def test_two_streams_in_flight(api):
         assert np.array_equal(host_pub[i].numpy(), want_pub.reshape(-1).cpu().numpy()), i
         assert host_priv[i].numpy().tobytes() == want_priv.cpu().numpy().tobytes(), i
         assert np.array_equal(host_out[i].numpy(), want_back.cpu().numpy()), i
+
+
+def test_more_streams_than_copy_lanes(api):
+    # 20 caller streams: 16 get their own copy streams, the rest share one pair; every call's
+    # results are still complete when its stream is
+    h, w, k = 64, 128, 5
+    pub_b, priv_b = api.sizes(w, h, k)
+    img = synth.make_image(w, h, 77)
+    key, iv = synth.make_key(78), synth.make_iv(79)
+    want_pub, want_priv = api.protect_image(torch.from_numpy(img).to(DEV), key, iv, k)
+    want_back = api.restore_image(want_pub, want_priv, w, h, k, key, iv).cpu().numpy()
+    host_in = torch.from_numpy(img).pin_memory()
+    runs = []
+    for _ in range(20):
+        s = torch.cuda.Stream(DEV)
+        r = dict(s=s, px=torch.empty((h, w, 3), dtype=torch.uint8, device=DEV),
+                 pub=torch.empty(pub_b // 2, dtype=torch.int16, device=DEV),
+                 priv=torch.empty(priv_b, dtype=torch.uint8, device=DEV),
+                 out=torch.empty((h, w, 3), dtype=torch.uint8, device=DEV),
+                 hpub=torch.empty(pub_b // 2, dtype=torch.int16).pin_memory(),
+                 hpriv=torch.empty(priv_b, dtype=torch.uint8).pin_memory(),
+                 hout=torch.empty((h, w, 3), dtype=torch.uint8).pin_memory())
+        runs.append(r)
+    torch.cuda.synchronize()
+    for r in runs:
+        with torch.cuda.stream(r["s"]):
+            api.protect_image_host(host_in, r["px"], key, iv, k, r["pub"], r["priv"], r["hpub"], r["hpriv"], 2)
+            api.restore_image_host(r["pub"], r["priv"], r["out"], r["hout"], key, iv, k, 2)
+    for r in runs:
+        r["s"].synchronize()                       # each stream alone covers its call's copies
+        assert np.array_equal(r["hpub"].numpy(), want_pub.reshape(-1).cpu().numpy())
+        assert r["hpriv"].numpy().tobytes() == want_priv.cpu().numpy().tobytes()
+        assert np.array_equal(r["hout"].numpy(), want_back)
