@@ -269,6 +269,16 @@ __device__ __forceinline__ void resolve_deferred(const TileArgs& a, uint2 e, int
 __device__ __forceinline__ void load_pixels(const TileSlot* sl, uint8_t* pix) {
   const uint64_t w3 = (uint64_t)sl->width * 3ull;
   const int nb = sl->nb;
+  if (sl->px_flags & kPxIn16) {              // whole rows of the tile: 16-byte pieces
+    constexpr int kPieces = kRowBytes / 16;
+    const uint8_t* row0 = sl->px_in + sl->blk[0];
+    for (int i = threadIdx.x; i < 8 * kPieces; i += kThreads) {
+      const int y = i / kPieces, x = i - y * kPieces;
+      cp_async16(pix + y * kRowBytes + 16 * x, row0 + y * w3 + 16 * x);
+    }
+    cp_async_commit();
+    return;
+  }
   for (int i = threadIdx.x; i < 8 * kTileBlocks * 3; i += kThreads) {
     const int y = i / (kTileBlocks * 3), rem = i - y * (kTileBlocks * 3);
     const int b = rem / 3, q = rem - 3 * b;

@@ -438,12 +438,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       // the pixel tile to global memory: one bulk (TMA engine) store per pixel row when the
       // tile's blocks are contiguous and 16-byte aligned in every row, else 8-byte stores
       const uint64_t w3 = (uint64_t)sl->width * 3ull;
-      const int bxc = sl->width >> 3;
-      const int bx0 = (sl->local * kTileBlocks) % bxc;
       uint8_t* row0 = sl->px_out + sl->blk[0];
-      const bool bulk = bx0 + nb <= bxc && ((nb * 24) & 15) == 0 && (w3 & 15) == 0 &&
-                        (reinterpret_cast<uintptr_t>(row0) & 15) == 0;
-      if (bulk) {
+      if (sl->px_flags & kPxOut16) {
         if (t == 0) {
 #pragma unroll 1
           for (int y = 0; y < 8; ++y) bulk_store(row0 + y * w3, pix + y * kRowBytes, (uint32_t)(nb * 24));

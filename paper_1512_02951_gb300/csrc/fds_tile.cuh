@@ -109,7 +109,11 @@ struct TileSlot {
   uint8_t* priv_out;
   uint64_t iv_hi, iv_lo;
   int32_t width, k, local, nb;    // local = tile index inside the image; nb = its blocks
+  // the tile's 8 pixel rows are contiguous runs of nb * 24 bytes in the image, 16-byte aligned
+  // (kPxIn16: in px_in, a whole tile; kPxOut16: in px_out)
+  int32_t px_flags;
 };
+constexpr int32_t kPxIn16 = 1, kPxOut16 = 2;
 
 // launchers (one translation unit each); `sms` = number of SMs of the device, `per_sm` =
 // resident CTAs per SM to launch (1 or 2)
@@ -245,6 +249,13 @@ __device__ __forceinline__ void fill_slot(const TileArgs& a, int g, TileSlot* s)
     s->k = k;
     s->local = local;
     s->nb = nb;
+    const int bxc = width >> 3;
+    const uint64_t w3 = 3ull * (uint64_t)width, b0 = block_offset(width, local * kTileBlocks);
+    const bool rows = (local * kTileBlocks) % bxc + nb <= bxc && ((nb * 24) & 15) == 0 && (w3 & 15) == 0;
+    int32_t f = 0;
+    if (rows && nb == kTileBlocks && (reinterpret_cast<uintptr_t>(a.pixels_in + pxo + b0) & 15) == 0) f |= kPxIn16;
+    if (rows && (reinterpret_cast<uintptr_t>(a.pixels_out + pxo + b0) & 15) == 0) f |= kPxOut16;
+    s->px_flags = f;
   }
   if (t < 44) s->rk[t] = rk[t];
   if (t < nb) s->blk[t] = block_offset(width, local * kTileBlocks + t);
