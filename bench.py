@@ -25,8 +25,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WIDTH = HEIGHT = 4096
-E2E_STRIPS = 2          # strips of the host-buffer pipeline (2 measured fastest of 1..8 with two lanes)
-E2E_LANES = 2           # steps in flight in the end-to-end measurement, one stream each
+E2E_STRIPS = 1          # strips of the host-buffer pipeline (1 measured fastest of 1..8 with three lanes)
+E2E_LANES = 3           # steps in flight in the end-to-end measurement, one stream each
 K_SEL = 5
 IMG_SEED, KEY_SEED, IV_SEED = 2, 2005, 3005
 METRIC = "protect+restore MB/s of pixels"
@@ -422,7 +422,7 @@ def gpu_arm(args):
             "e2e": {"value": round(world * px_bytes / (e2e_ms * 1e-3) / 1e6, 1), "unit": UNIT,
                     "h2d_bytes_per_step": px_bytes,
                     "d2h_bytes_per_step": pub_b + priv_b + px_bytes,
-                    "note": f"fds_protect_image_host + fds_restore_image_host: H2D pixels, protect, D2H both fragments, restore, D2H pixels, in {E2E_STRIPS} strips, {E2E_LANES} steps in flight on {E2E_LANES} streams with their own buffers; the D2H bytes bound it (host link measured at 193 GB/s device to host, 211 GB/s host to device, 167 GB/s each way together)"},
+                    "note": f"fds_protect_image_host + fds_restore_image_host: H2D pixels, protect, D2H both fragments, restore, D2H pixels, in {E2E_STRIPS} strip{'s' if E2E_STRIPS > 1 else ''} per call, {E2E_LANES} steps in flight on {E2E_LANES} streams with their own buffers; the D2H bytes bound it (host link measured at 193 GB/s device to host, 211 GB/s host to device, 167 GB/s each way together)"},
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
             "quality": {"exact_restore_fraction": round(exact_frac, 5), "psnr_db": round(psnr, 3),
