@@ -377,6 +377,20 @@ int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound
 int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height,
                      float* coefs_out, void* stream);
 
+/* Diagnostics: the exact rounding step of both transforms on its own (Sect. 6.4.3 reading:
+ * round half away from zero of the exact value).  For each i, with c(j) = cos(j pi / 16),
+ *   8 V_i = coords[8i] + sum_{j=1..7} coords[8i + j] c(j),
+ * out[i] = V_i rounded half away from zero, decided exactly: a 64-bit fixed-point evaluation
+ * first and, where it is too close to call, a 256-bit one that a norm bound in Z[cos(pi/16)]
+ * makes exact.  This is the routine the fused kernels call for every value within their
+ * float32 error guard of a half-integer; the 256-bit evaluations it needed are added to
+ * counter 1 of fds_counters, failures (none can occur) to counter 2.
+ * coords: host int32 [n][8]; out: host int32 [n].  Every vector must satisfy |coords[8i]| <
+ * 2^26 and sum_j |coords[8i + j]| < 2^26 (the proven range; the kernels' own coordinates
+ * stay below 2^23), else FDS_E_INVALID and nothing runs.  Synchronous; allocates and frees
+ * its own device buffer. */
+int fds_debug_exact_round(const int32_t* coords, int32_t* out, int32_t n);
+
 /* Diagnostics: counters of the exact-rounding fallbacks taken since the last reset:
  * out[0] = values within the float32 error guard of a rounding boundary, re-decided from
  * their exact integer coordinates in Z[cos(pi/16)]; out[1] = of those, values whose 128-bit

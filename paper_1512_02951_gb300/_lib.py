@@ -129,6 +129,8 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_double)]),
     "fds_debug_dct_tc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "fds_debug_exact_round": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_int32]),
     "fds_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "fds_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "fds_last_error": (ctypes.c_char_p, []),

@@ -464,6 +464,19 @@ def debug_dct_tc(pixels: torch.Tensor, form: str = "bf16") -> torch.Tensor:
     return out
 
 
+def debug_exact_round(coords) -> list[int]:
+    """fds_debug_exact_round (host in, host out): the device's exact round-half-away of V_i
+    with 8 V_i = coords[i][0] + sum_j coords[i][j] cos(j pi/16), for an n x 8 integer array."""
+    flat = [int(v) for row in coords for v in row]
+    n = len(flat) // 8
+    if len(flat) != 8 * n:
+        raise ValueError("coords must be rows of 8 integers")
+    cin = (ctypes.c_int32 * max(1, len(flat)))(*flat)
+    out = (ctypes.c_int32 * max(1, n))()
+    _lib.check(_lib.load().fds_debug_exact_round(cin, out, n), "fds_debug_exact_round")
+    return [int(out[i]) for i in range(n)]
+
+
 def counters(reset: bool = False) -> tuple[int, int, int]:
     """fds_counters: (exact re-decisions, 256-bit escalations among them, failures)."""
     out = (ctypes.c_uint64 * 3)()

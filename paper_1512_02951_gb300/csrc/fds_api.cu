@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -35,6 +36,24 @@ __device__ unsigned long long g_counters[3];
 //  g_tcb0/1   tensor-core B operands (basis limbs, BF16 / TF32) in shared-memory byte order
 __device__ __align__(16) uint4 g_tcb0[kTcBBytesBf16 / 16];
 __device__ __align__(16) uint4 g_tcb1[kTcBBytesTf32 / 16];
+
+// The exact rounding step alone: out[i] = round half away from zero of V_i, 8 V_i =
+// coords[8i] + sum_j coords[8i + j] cos(j pi/16); escalations and failures are counted like
+// the fused kernels count them
+__global__ void debug_exact_round_kernel(const int32_t* coords, int32_t* out, int32_t n,
+                                         unsigned long long* counters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[9];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) c[j] = coords[8 * i + j];
+  c[8] = 0;
+  int esc = 0;
+  bool fail = false;
+  out[i] = exact_round(c, &esc, &fail);
+  if (esc) atomicAdd(&counters[1], (unsigned long long)esc);
+  if (fail) atomicAdd(&counters[2], 1ull);
+}
 
 __global__ void init_tables_kernel() {
   const int t = threadIdx.x;
@@ -1020,6 +1039,35 @@ int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core debug launch");
 }
 
+int fds_debug_exact_round(const int32_t* coords, int32_t* out, int32_t n) {
+  if (n < 0) return set_err(FDS_E_INVALID, "negative count");
+  if (n > 0 && (!coords || !out)) return set_err(FDS_E_INVALID, "null pointer argument");
+  // the range in which the device decision is proven exact (the fused kernels stay far
+  // inside it): |N_0| < 2^26 and sum_j>=1 |N_j| < 2^26
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t s = 0;
+    for (int j = 1; j < 8; ++j) s += std::llabs((int64_t)coords[8 * i + j]);
+    if (std::llabs((int64_t)coords[8 * i]) >= (1ll << 26) || s >= (1ll << 26))
+      return set_err(FDS_E_INVALID, "coordinate vector " + std::to_string(i) + " outside |N_0|, sum |N_j| < 2^26");
+  }
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  if (n == 0) return FDS_OK;
+  int32_t* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int32_t) * 9ull * (size_t)n);
+  if (e != cudaSuccess) return set_err(FDS_E_NOMEM, "device allocation failed");
+  e = cudaMemcpy(d, coords, sizeof(int32_t) * 8ull * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    debug_exact_round_kernel<<<(n + 127) / 128, 128>>>(d, d + 8ull * (size_t)n, n, g_tables[dev].counters);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 8ull * (size_t)n, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost);
+  const cudaError_t ef = cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "exact-round diagnostic");
+  return ef == cudaSuccess ? FDS_OK : cuda_fail(ef, "cudaFree");
+}
+
 int fds_counters(uint64_t* out, int reset) {
   if (!out) return set_err(FDS_E_INVALID, "null output");
   int rc = ensure_init();
@@ -1428,8 +1476,26 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 unsigned char* g_noalloc_addr[kMaxDevices];   // device address of the scratch, per device
-constexpr int kNoAllocChunk = 128;            // descriptors staged per host->device copy
 }  // namespace
+
+// One chunk of the batch's tables, passed BY VALUE as a kernel parameter (under the 4 KB
+// parameter limit), so that nothing depends on the lifetime of a host buffer: the values
+// are captured when the launch is enqueued.
+constexpr int kNoAllocChunk = 64;
+struct NoAllocChunk {
+  BatchImage img[kNoAllocChunk];
+  int32_t ts[kNoAllocChunk + 1];
+  int32_t first, count, ts_count, reset_counter;
+};
+static_assert(sizeof(NoAllocChunk) <= 4000, "kernel parameter limit");
+
+__global__ void noalloc_upload_kernel(const __grid_constant__ NoAllocChunk c, BatchImage* img, int32_t* ts,
+                                      unsigned int* counter) {
+  const int t = threadIdx.x;
+  if (t < c.count) img[c.first + t] = c.img[t];
+  if (t < c.ts_count) ts[c.first + t] = c.ts[t];
+  if (t == 0 && c.reset_counter) *counter = 0u;   // the tile counter must start at zero
+}
 
 }  // namespace fds
 
@@ -1445,6 +1511,12 @@ extern "C" int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_
     if ((rc = check_descs(images, n))) return rc;
   }
   if ((rc = plan_buffers_ok(pixels, public_out, private_out))) return rc;
+  {   // the whole batch is checked before anything is enqueued
+    int64_t tiles = 0;
+    for (int32_t i = 0; i < n; ++i)
+      tiles += ((int64_t)(images[i].width / 8) * (images[i].height / 8) + kTileBlocks - 1) / kTileBlocks;
+    if (tiles > (1ll << 30)) return set_err(FDS_E_INVALID, "batch too large");
+  }
   int dev = 0;
   if ((rc = ensure_init(&dev))) return rc;
   unsigned char* base;
@@ -1462,16 +1534,16 @@ extern "C" int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_
   BatchImage* d_img = reinterpret_cast<BatchImage*>(base);
   int32_t* d_ts = reinterpret_cast<int32_t*>(base + kNoAllocImgBytes);
   unsigned int* d_counter = reinterpret_cast<unsigned int*>(base + kNoAllocImgBytes + kNoAllocTsBytes);
-  // descriptors and tile prefix sums, staged through small host buffers on the stack
-  BatchImage bi[kNoAllocChunk];
-  int32_t ts[kNoAllocChunk + 1];
+  // descriptors and tile prefix sums, chunk by chunk as kernel parameters
+  NoAllocChunk c;
   int64_t acc = 0;
   int32_t k_uniform = images[0].k;
   for (int32_t c0 = 0; c0 < n; c0 += kNoAllocChunk) {
     const int32_t m = std::min<int32_t>(kNoAllocChunk, n - c0);
+    std::memset(&c, 0, sizeof(c));
     for (int32_t j = 0; j < m; ++j) {
       const fds_image& d = images[c0 + j];
-      BatchImage& b = bi[j];
+      BatchImage& b = c.img[j];
       b.pixel_offset = d.pixel_offset;
       b.public_offset = d.public_offset;
       b.private_offset = d.private_offset;
@@ -1481,20 +1553,19 @@ extern "C" int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_
       b.key_slot = d.key_slot;
       iv_words(d.iv, &b.iv_hi, &b.iv_lo);
       if (d.k != k_uniform) k_uniform = -1;
-      ts[j] = (int32_t)acc;
+      c.ts[j] = (int32_t)acc;
       acc += ((int64_t)(d.width / 8) * (d.height / 8) + kTileBlocks - 1) / kTileBlocks;
-      if (acc > (1ll << 30)) return set_err(FDS_E_INVALID, "batch too large");
     }
-    const int32_t extra = (c0 + m == n) ? 1 : 0;   // the last chunk also writes tile_start[n]
-    if (extra) ts[m] = (int32_t)acc;
-    // pageable source: the copy has consumed the stack buffer when the call returns
-    cudaError_t e = cudaMemcpyAsync(d_img + c0, bi, sizeof(BatchImage) * m, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_ts + c0, ts, sizeof(int32_t) * (m + extra), cudaMemcpyHostToDevice, s);
+    const bool last = c0 + m == n;                 // the last chunk also writes tile_start[n]
+    if (last) c.ts[m] = (int32_t)acc;
+    c.first = c0;
+    c.count = m;
+    c.ts_count = m + (last ? 1 : 0);
+    c.reset_counter = last ? 1 : 0;
+    noalloc_upload_kernel<<<1, kNoAllocChunk + 1, 0, s>>>(c, d_img, d_ts, d_counter);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "scratch upload");
   }
-  const cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s);   // must start at 0
-  if (e != cudaSuccess) return cuda_fail(e, "counter reset");
   TileArgs a{};
   a.pixels_in = pixels;
   a.pub_out = public_out;

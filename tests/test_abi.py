@@ -204,3 +204,13 @@ def test_dwt_sizes_and_checks(lib):
     assert lib.fds_dwt_protect(None, 64, 48, key, key, 16, 16, 16, None) != 0
     assert lib.fds_dwt_protect(16, 64, 48, key, key, 16, 24, 16, None) != 0     # misaligned level 2
     assert lib.fds_dwt_restore(16, 16, 16, 64, 44, key, key, 16, None) != 0      # H not a multiple of 8
+
+
+def test_exact_round_diagnostic_rejects_vectors_outside_the_proven_range(lib):
+    # the range check runs on the host before any device work
+    bad = (ctypes.c_int32 * 8)(1 << 26, 0, 0, 0, 0, 0, 0, 0)
+    out = (ctypes.c_int32 * 1)()
+    assert lib.fds_debug_exact_round(bad, out, 1) == -1
+    bad2 = (ctypes.c_int32 * 8)(0, 1 << 25, -(1 << 25), 0, 0, 0, 0, 0)
+    assert lib.fds_debug_exact_round(bad2, out, 1) == -1
+    assert lib.fds_debug_exact_round(None, None, -1) == -1

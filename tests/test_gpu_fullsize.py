@@ -1,0 +1,180 @@
+"""Whole-output parity at the benchmark sizes, through the C ABI, against the CPU oracle.
+
+  * the 4096 x 4096 RGB image (the benchmark workload) at k = 0 and k = 5: every public int16,
+    every ciphertext byte and every restored pixel, for the float32 CUDA-core kernels and for
+    both tensor-core forms of protect;
+  * the per-block float32 error guard of the protect kernel, u (2.7 V + 0.9 W + 1), on every
+    channel-block of that image and of a 200-image batch of uneven sizes;
+  * the batched plan (one persistent launch per direction over a 2000-image batch of uneven
+    sizes): every byte of a seeded subset of 40 images against the oracle, the rest against
+    the per-image launches.
+
+Rounding is half away from zero of the exact value (the reading of Sect. 6.4.3), so every
+output is a pure function of the input and the comparison is for equality."""
+import numpy as np
+import pytest
+
+from oracle import dct as odct, fds as ofds
+from paper_1512_02951_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+W = H = 4096
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_02951_gb300 import api as _api, build
+
+    build.build()
+    _api.init(0)
+    _api.counters(reset=True)
+    yield _api
+    assert _api.counters()[2] == 0, "exact-rounding consistency failure or lost wait"
+
+
+_ORACLE = {}
+
+
+def _oracle(k):
+    """Oracle protect + restore of the 4096^2 workload image at selection k (cached)."""
+    if k not in _ORACLE:
+        img = synth.make_image(W, H, 2)
+        key, iv = synth.make_key(2000 + k), synth.make_iv(3000 + k)
+        pub, priv = ofds.protect(img, key, iv, k)
+        back = ofds.restore(pub, priv, key, iv, k, W, H)
+        _ORACLE[k] = (img, key, iv, pub, priv, back)
+    return _ORACLE[k]
+
+
+def _first_diff(a, b):
+    bad = np.argwhere(a != b)
+    return f"{len(bad)} mismatches, first {bad[:4].tolist()}"
+
+
+@pytest.mark.parametrize("k", [0, 5])
+def test_4096_whole_image_bit_exact(api, k):
+    img, key, iv, want_pub, want_priv, want_back = _oracle(k)
+    x = torch.from_numpy(img).to(DEV)
+    pub, priv = api.protect_image(x, key, iv, k)
+    back = api.restore_image(pub, priv, W, H, k, key, iv)
+    torch.cuda.synchronize()
+    pub_h, priv_h, back_h = pub.cpu().numpy(), priv.cpu().numpy().tobytes(), back.cpu().numpy()
+    assert np.array_equal(pub_h, want_pub), _first_diff(pub_h, want_pub)
+    assert priv_h == want_priv, "private ciphertext differs"
+    assert np.array_equal(back_h, want_back), _first_diff(back_h, want_back)
+    assert 0.88 < np.mean(back_h == img) < 0.97
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+@pytest.mark.parametrize("k", [0, 5])
+def test_4096_whole_image_tensor_core_forms_bit_exact(api, form, k):
+    img, key, iv, want_pub, want_priv, _ = _oracle(k)
+    pub, priv = api.protect_image_tc(torch.from_numpy(img).to(DEV), key, iv, k, form)
+    torch.cuda.synchronize()
+    pub_h = pub.cpu().numpy()
+    assert np.array_equal(pub_h, want_pub), _first_diff(pub_h, want_pub)
+    assert priv.cpu().numpy().tobytes() == want_priv, f"{form}: private ciphertext differs"
+
+
+def _pass_weight(x):
+    d = np.abs(x[..., :4] - x[..., 7:3:-1]).sum(axis=-1)
+    s = x[..., :4] + x[..., 7:3:-1]
+    return d + np.abs(s[..., 0] - s[..., 3]) + np.abs(s[..., 1] - s[..., 2])
+
+
+def _guard_violations(api, img):
+    """Channel-blocks whose float32 pre-rounding error exceeds the kernel's per-block guard
+    u (2.7 V + 0.9 W + 1) (V: error weight of the row passes, W: of columns 0 and 4); also
+    returns the largest error / guard ratio."""
+    got = api.debug_dct_f32(torch.from_numpy(np.ascontiguousarray(img)).to(DEV)).cpu().numpy()
+    blocks = odct.image_to_blocks(img).astype(np.int64)
+    worst, nbad = 0.0, 0
+    for r0 in range(0, blocks.shape[0], 64):                      # block-row strips bound memory
+        b = blocks[r0: r0 + 64]
+        V = _pass_weight(b).sum(axis=-1)
+        x = b - 128
+        col0 = x.sum(axis=-1)
+        col4 = x[..., [0, 3, 4, 7]].sum(axis=-1) - x[..., [1, 2, 5, 6]].sum(axis=-1)
+        Wt = _pass_weight(col0) + _pass_weight(col4)
+        bound = 2.0 ** -24 * (2.7 * V + 0.9 * Wt + 1)
+        err = np.abs(got[r0: r0 + 64].astype(np.float64) - odct.dct2(b)).max(axis=(-1, -2))
+        worst = max(worst, float((err / bound).max()))
+        nbad += int((err > bound).sum())
+    return nbad, worst
+
+
+def test_guard_holds_on_every_block_of_the_4096_image(api):
+    nbad, worst = _guard_violations(api, synth.make_image(W, H, 2))
+    assert nbad == 0, (nbad, worst)
+    assert worst < 1.0
+
+
+def test_guard_holds_on_a_200_image_batch(api):
+    worst = 0.0
+    for i, (w, h) in enumerate(synth.batch_sizes(200, 4242)):
+        nbad, r = _guard_violations(api, synth.make_image(w, h, 60000 + i))
+        assert nbad == 0, (i, w, h, nbad, r)
+        worst = max(worst, r)
+    assert worst < 1.0
+
+
+def test_plan_2000_images_against_oracle_and_per_image(api):
+    import bench
+
+    sizes, crops = bench.batch_inputs(2000, 1000)
+    descs, keys = [], []
+    for i, (w, h) in enumerate(sizes):
+        key = synth.make_key(7000 + i % 64)
+        keys.append(key)
+        descs.append(api.ImageDesc(w, h, 0 if i % 3 else 5, -1, synth.make_iv(9000 + i)))
+    slots = {}
+    for d, key in zip(descs, keys):
+        if key not in slots:
+            slots[key] = api.key_register(key)
+        d.key_slot = slots[key]
+    npx, npub, npriv = api.layout(descs)
+    px_h = np.zeros(npx, dtype=np.uint8)
+    imgs = []
+    for d, (b, y0, x0, w, h) in zip(descs, crops):
+        im = np.ascontiguousarray(b[y0: y0 + h, x0: x0 + w])
+        imgs.append(im)
+        px_h[d.pixel_offset: d.pixel_offset + im.size] = im.reshape(-1)
+    px = torch.from_numpy(px_h).to(DEV)
+    pub = torch.zeros(npub, dtype=torch.uint8, device=DEV)
+    priv = torch.zeros(npriv, dtype=torch.uint8, device=DEV)
+    back = torch.zeros_like(px)
+    plan = api.Plan(descs)
+    plan.protect(px, pub, priv)
+    plan.restore(pub, priv, back)
+    pub2 = torch.zeros_like(pub)
+    priv2 = torch.zeros_like(priv)
+    back2 = torch.zeros_like(px)
+    api.protect(px, pub2, priv2, descs)
+    api.restore(pub2, priv2, back2, descs)
+    torch.cuda.synchronize()
+    pub_h, priv_h, back_h = pub.cpu().numpy(), priv.cpu().numpy(), back.cpu().numpy()
+    pub2_h, priv2_h, back2_h = pub2.cpu().numpy(), priv2.cpu().numpy(), back2.cpu().numpy()
+    plan.close()
+    rng = np.random.default_rng(31)
+    subset = set(int(i) for i in rng.choice(len(descs), 40, replace=False))
+    for i, d in enumerate(descs):
+        pb, vb = ofds.sizes(d.width, d.height, d.k)
+        n = d.width * d.height * 3
+        gp = pub_h[d.public_offset: d.public_offset + pb]
+        gv = priv_h[d.private_offset: d.private_offset + vb]
+        gb = back_h[d.pixel_offset: d.pixel_offset + n]
+        assert np.array_equal(gp, pub2_h[d.public_offset: d.public_offset + pb]), i
+        assert np.array_equal(gv, priv2_h[d.private_offset: d.private_offset + vb]), i
+        assert np.array_equal(gb, back2_h[d.pixel_offset: d.pixel_offset + n]), i
+        if i in subset:
+            want_pub, want_priv = ofds.protect(imgs[i], keys[i], d.iv, d.k)
+            assert gp.tobytes() == want_pub.tobytes(), i
+            assert gv.tobytes() == want_priv, i
+            want = ofds.restore(want_pub, want_priv, keys[i], d.iv, d.k, d.width, d.height)
+            assert np.array_equal(gb.reshape(imgs[i].shape), want), i
+    for s in slots.values():
+        api.key_release(s)

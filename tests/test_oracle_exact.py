@@ -167,6 +167,24 @@ def test_exact_sign_against_high_precision():
     assert exact.exact_sign(0, [0] * 7) == 0
 
 
+def test_near_relations_fixture_is_tiny_nonzero_and_signed_right():
+    # tests/golden/exact_near_relations.txt: N_0 + sum_j N_j cos(j pi/16) nonzero, tiny, its
+    # sign the oracle's, and -- shifted onto a half-integer boundary -- closer to it than a
+    # 64-bit fixed-point evaluation can resolve (what makes the device escalate)
+    from conftest import read_golden
+    mp = _mp()
+    mp.mp.dps = 60
+    cs = [mp.cos(j * mp.pi / 16) for j in range(8)]
+    rows = [[int(t) for t in ln.split("#")[0].split()] for ln in read_golden("exact_near_relations.txt")]
+    assert len(rows) >= 24
+    for n in rows:
+        val = n[0] + sum(n[j] * cs[j] for j in range(1, 8))
+        assert mp.mpf(2) ** -100 < abs(val) < mp.mpf(2) ** -55
+        assert exact.exact_sign(n[0], n[1:]) == (1 if val > 0 else -1)
+        assert sum(abs(t) for t in n[1:]) * mp.mpf(2) ** -62 > abs(val)   # below the 64-bit error bound
+        assert max(abs(t) for t in n) <= 32640                            # forward-transform range
+
+
 def test_forward_rounding_against_brute_force():
     mp = _mp()
     rng = np.random.default_rng(15)
