@@ -18,6 +18,7 @@ FDS_MAX_KEYS = 256
 FDS_NOALLOC_MAX_IMAGES = 4096
 FDS_TC_BF16 = 0
 FDS_TC_TF32 = 1
+FDS_TC_F16 = 2
 FDS_PACK_11 = 11
 FDS_PACK_8 = 8
 

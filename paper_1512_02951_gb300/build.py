@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfds.so")
-UNITS = ("fds_api", "fds_protect", "fds_restore", "fds_protect_tc", "fds_aes_full", "fds_pack", "fds_stats", "fds_strong", "fds_dwt")
+UNITS = ("fds_api", "fds_protect", "fds_restore", "fds_protect_tc", "fds_protect_mma", "fds_aes_full", "fds_pack", "fds_stats", "fds_strong", "fds_dwt")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                  "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

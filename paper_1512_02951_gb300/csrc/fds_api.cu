@@ -36,6 +36,9 @@ __device__ unsigned long long g_counters[3];
 //  g_tcb0/1   tensor-core B operands (basis limbs, BF16 / TF32) in shared-memory byte order
 __device__ __align__(16) uint4 g_tcb0[kTcBBytesBf16 / 16];
 __device__ __align__(16) uint4 g_tcb1[kTcBBytesTf32 / 16];
+//  g_mma_fwd  B operand of the warp-specialised tensor-core protect (f16, two limbs, rows in
+//             zigzag order), in shared-memory byte order
+__device__ __align__(16) uint4 g_mma_fwd[16384 / 16];
 
 // The exact rounding step alone: out[i] = round half away from zero of V_i, 8 V_i =
 // coords[8i] + sum_j coords[8i + j] cos(j pi/16); escalations and failures are counted like
@@ -80,6 +83,8 @@ struct DevTables {
   const uint32_t* round_keys;
   unsigned long long* counters;
   const uint4* tc_b[2];
+  const uint4* mma_fwd;
+  float mma_fwd_guard;
   int sms;
 };
 DevTables g_tables[kMaxDevices];
@@ -193,6 +198,68 @@ bool build_tc_b(int form, std::vector<uint8_t>& img, std::string& why, double* b
   return true;
 }
 
+// f16 bit pattern of an integer |v| <= 2048 (exact)
+uint16_t f16_of_int(int v) {
+  if (v == 0) return 0;
+  const uint16_t sign = v < 0 ? 0x8000u : 0u;
+  unsigned m = (unsigned)(v < 0 ? -v : v);
+  int e = 0;
+  while ((m >> e) > 1) ++e;                            // m in [2^e, 2^(e+1))
+  const unsigned frac = (m << (10 - e)) & 0x3FFu;      // exact: m has at most 11 significant bits
+  return (uint16_t)(sign | (unsigned)((e + 15) << 10) | frac);
+}
+
+// B operand of the tensor-core protect (f16, two limbs): row n = 64 l + z holds limb l of
+// 2^13 b_u(y) b_v(x) ((u, v) the zigzag position z) at K index 8y + x, split as L0 + L1 2^-11
+// with integer limbs, laid out as the kernel's 128-byte swizzled K-major shared-memory image.
+// Returns false (with a message) unless the kernel's exactness argument holds: limbs exact in
+// f16, every accumulator an integer below 2^24 for inputs |p - 128| <= 128, the rational
+// coefficients carried by limb 0 alone.  *bound: a proven bound on |computed - exact| of a
+// pre-rounding coefficient (limb remainder over |p - 128| <= 128, plus half an ulp of the one
+// rounding t = D0 + D1 2^-11 with |t| < 2^23, plus the error of cos() in double).
+bool build_mma_fwd(std::vector<uint8_t>& img, double* bound, std::string& why) {
+  img.assign(16384, 0);
+  double b[8][8];
+  for (int u = 0; u < 8; ++u)
+    for (int y = 0; y < 8; ++y) b[u][y] = (u == 0 ? std::sqrt(0.5) : 1.0) * 0.5 * std::cos((2 * y + 1) * u * std::acos(-1.0) / 16);
+  int uz[64], vz[64];
+  for (int u = 0; u < 8; ++u)
+    for (int v = 0; v < 8; ++v) uz[zigzag_of(u, v)] = u, vz[zigzag_of(u, v)] = v;
+  double rem_max = 0, fmax = 0;
+  for (int z = 0; z < 64; ++z) {
+    const int u = uz[z], v = vz[z];
+    const bool rational = (u == 0 || u == 4) && (v == 0 || v == 4);
+    double rem = 0, fsum = 0, lsum[2] = {0, 0};
+    for (int kk = 0; kk < 64; ++kk) {
+      const double B = b[u][kk >> 3] * b[v][kk & 7];
+      fsum += std::fabs(B);
+      double r = std::ldexp(B, 13);
+      const double L0 = std::nearbyint(r);
+      r = std::ldexp(r - L0, 11);
+      const double L1 = std::nearbyint(r);
+      rem += std::ldexp(std::fabs(r - L1), -24);
+      const double L[2] = {L0, L1};
+      for (int l = 0; l < 2; ++l) {
+        if (std::fabs(L[l]) > 2048.0) return (why = "limb not exact in f16"), false;
+        lsum[l] += std::fabs(L[l]);
+        const int n = 64 * l + z;
+        const uint16_t h = f16_of_int((int)L[l]);
+        std::memcpy(&img[n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2], &h, 2);
+      }
+      if (rational && (std::fabs(L0) != 1024.0 || L1 != 0.0))
+        return (why = "rational coefficient not carried by limb 0 alone"), false;
+    }
+    for (int l = 0; l < 2; ++l)
+      if (128.0 * lsum[l] >= 16777216.0) return (why = "accumulator may exceed 2^24"), false;
+    rem_max = std::max(rem_max, 128.0 * rem);
+    if (!rational) fmax = std::max(fmax, 128.0 * fsum);
+  }
+  if (fmax * 8192.0 >= 8388608.0) return (why = "a coefficient may exceed 2^23 in units of 2^-13"), false;
+  *bound = rem_max + std::ldexp(1.0, -14) + 64.0 * 255.0 * std::ldexp(1.0, -50);
+  if (*bound >= 1.0 / 1024) return (why = "limb split too coarse"), false;
+  return true;
+}
+
 // Initialise the current device (once) and return its index in *dev_out.
 int ensure_init(int* dev_out = nullptr) {
   int dev = 0;
@@ -283,6 +350,19 @@ int ensure_init(int* dev_out = nullptr) {
     tb.tc_b[0] = static_cast<const uint4*>(p);
     if ((e = cudaGetSymbolAddress(&p, g_tcb1)) != cudaSuccess) return cuda_fail(e, "symbol address");
     tb.tc_b[1] = static_cast<const uint4*>(p);
+  }
+  {
+    static std::vector<uint8_t> mf;
+    static double mf_bound = 0;
+    static bool mf_ok = false;
+    static std::string mf_why;
+    if (mf.empty()) mf_ok = build_mma_fwd(mf, &mf_bound, mf_why);
+    if (!mf_ok) return set_err(FDS_E_INVALID, "tensor-core table: " + mf_why);
+    if ((e = cudaMemcpyToSymbol(g_mma_fwd, mf.data(), mf.size())) != cudaSuccess) return cuda_fail(e, "table upload");
+    if ((e = cudaGetSymbolAddress(&p, g_mma_fwd)) != cudaSuccess) return cuda_fail(e, "symbol address");
+    tb.mma_fwd = static_cast<const uint4*>(p);
+    // the guard the kernel compares with, rounded up: float(bound) * (1 + 2^-20)
+    tb.mma_fwd_guard = (float)(mf_bound * (1.0 + std::ldexp(1.0, -20)));
   }
   if ((e = upload_sha512_constants()) != cudaSuccess) return cuda_fail(e, "SHA-512 constants upload");
   if ((e = upload_dwt_constants()) != cudaSuccess) return cuda_fail(e, "SHA constants upload");
@@ -497,7 +577,10 @@ int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height, floa
 int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height, int32_t k,
                          const uint8_t key[16], const uint8_t iv[16], int16_t* public_out,
                          uint8_t* private_out, void* stream) {
-  if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32 && form != FDS_TC_F16)
+    return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  if (form == FDS_TC_F16 && k >= 0 && k <= 63 && !mma_supports_k(k))
+    return set_err(FDS_E_INVALID, "FDS_TC_F16 takes k = " + std::string(FDS_TC_F16_K_LIST));
   if (bad_dims(width, height) || 3ll * (width / 8) * (height / 8) >= (1ll << 31))
     return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8, 3 W H / 64 < 2^31");
   if (k < 0 || k > 63) return set_err(FDS_E_INVALID, "k must be in 0..63");
@@ -516,8 +599,14 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
   expand_key(key, a.rk);
   iv_words(iv, &a.iv_hi, &a.iv_lo);
   set_tables(a, dev);
-  a.tc_b = g_tables[dev].tc_b[form];
-  const cudaError_t e = launch_protect_tc(a, (cudaStream_t)stream, form, false, g_tables[dev].sms);
+  cudaError_t e;
+  if (form == FDS_TC_F16) {
+    e = launch_protect_mma(a, g_tables[dev].mma_fwd, g_tables[dev].mma_fwd_guard, (cudaStream_t)stream, false,
+                           g_tables[dev].sms);
+  } else {
+    a.tc_b = g_tables[dev].tc_b[form];
+    e = launch_protect_tc(a, (cudaStream_t)stream, form, false, g_tables[dev].sms);
+  }
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core protect launch");
 }
 
@@ -1005,11 +1094,12 @@ int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]) {
 }
 
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {
-  if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32 && form != FDS_TC_F16)
+    return set_err(FDS_E_INVALID, "unknown tensor-core form");
   std::vector<uint8_t> img;
   std::string why;
   double bound = 0;
-  const bool ok = build_tc_b(form, img, why, &bound);
+  const bool ok = form == FDS_TC_F16 ? build_mma_fwd(img, &bound, why) : build_tc_b(form, img, why, &bound);
   if (error_bound) *error_bound = bound;
   if (!ok) return set_err(FDS_E_INVALID, "tensor-core table: " + why);
   if (out) {
@@ -1021,7 +1111,8 @@ int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound
 
 int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height, float* coefs_out,
                      void* stream) {
-  if (form != FDS_TC_BF16 && form != FDS_TC_TF32) return set_err(FDS_E_INVALID, "unknown tensor-core form");
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32 && form != FDS_TC_F16)
+    return set_err(FDS_E_INVALID, "unknown tensor-core form");
   if (bad_dims(width, height) || 3ll * (width / 8) * (height / 8) >= (1ll << 31))
     return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8, 3 W H / 64 < 2^31");
   if (!pixels || !coefs_out) return set_err(FDS_E_INVALID, "null pointer argument");
@@ -1034,8 +1125,14 @@ int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t
   a.dbg_coefs = coefs_out;
   fill_geometry(a, width, height, 0);
   set_tables(a, dev);
-  a.tc_b = g_tables[dev].tc_b[form];
-  const cudaError_t e = launch_protect_tc(a, (cudaStream_t)stream, form, true, g_tables[dev].sms);
+  cudaError_t e;
+  if (form == FDS_TC_F16) {
+    e = launch_protect_mma(a, g_tables[dev].mma_fwd, g_tables[dev].mma_fwd_guard, (cudaStream_t)stream, true,
+                           g_tables[dev].sms);
+  } else {
+    a.tc_b = g_tables[dev].tc_b[form];
+    e = launch_protect_tc(a, (cudaStream_t)stream, form, true, g_tables[dev].sms);
+  }
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core debug launch");
 }
 

@@ -177,15 +177,26 @@ constexpr uint32_t kMbarSpinLimit = 1u << 22;   // bounded waits (seconds at mos
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
 }
-// bounded wait for phase `parity`; false if it did not complete in time
+// bounded wait for phase `parity`; false if it did not complete in time (about 2 s of wall
+// clock, or kMbarSpinLimit polls)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok = 0;
-  for (uint32_t i = 0; i < kMbarSpinLimit && !ok; ++i)
+  uint64_t t0 = 0;
+  for (uint32_t i = 0; i < kMbarSpinLimit && !ok; ++i) {
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  "selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok)
                  : "r"(smem_u32(bar)), "r"(parity)
                  : "memory");
+    if (!ok && (i & 255u) == 0u) {
+      uint64_t now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (i == 0)
+        t0 = now;
+      else if (now - t0 > 2000000000ull)
+        break;
+    }
+  }
   return ok != 0;
 }
 // the one arrival of the phase, announcing `bytes` of bulk loads

@@ -11,7 +11,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
-FORMS = ["bf16", "tf32"]
+FORMS = ["bf16", "tf32", "f16"]
+F16_K = {0, 5}                   # selections the f16 (warp-specialised) form is built for
+
+
+def _skip_unsupported(form, k):
+    if form == "f16" and k not in F16_K:
+        pytest.skip("selection not instantiated for the f16 form")
 
 
 @pytest.fixture(scope="module")
@@ -46,6 +52,7 @@ def _check(api, img, k, form, seed=0):
 @pytest.mark.parametrize("w,h", [(8, 8), (16, 8), (64, 64), (136, 72), (520, 40)])
 @pytest.mark.parametrize("k", [0, 5, 63])
 def test_tc_small_and_ragged_images(api, form, w, h, k):
+    _skip_unsupported(form, k)
     # 3 .. 975 channel-blocks: one partial tile, and several 128-channel-block tiles that
     # straddle pixel blocks and block rows, with a ragged last tile
     _check(api, synth.make_image(w, h, w * 5 + h), k, form, seed=w + h + k)
@@ -54,6 +61,7 @@ def test_tc_small_and_ragged_images(api, form, w, h, k):
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("k", [0, 5, 17])
 def test_tc_512_generator_image(api, form, k):
+    _skip_unsupported(form, k)
     _check(api, synth.make_image(512, 512, 1), k, form, seed=k)
 
 

@@ -11,7 +11,15 @@ import pytest
 from oracle import dct as odct
 
 # form -> (limb shifts, rounding guard, largest limb exact in the operand type)
-FORMS = {"bf16": ((9, 8, 8), 2.0 ** -11, 256), "tf32": ((12, 11), 2.0 ** -10, 2048)}
+FORMS = {"bf16": ((9, 8, 8), 2.0 ** -11, 256), "tf32": ((12, 11), 2.0 ** -10, 2048),
+         "f16": ((13, 11), 2.0 ** -10, 2048)}
+# the f16 form holds its rows in zigzag order and its A operand is p - 128 (|.| <= 128)
+PIXEL_BOUND = {"bf16": 255, "tf32": 255, "f16": 128}
+
+
+def _zigzag():
+    from oracle import fds as ofds
+    return [8 * u + v for (u, v) in ofds.ZIGZAG]
 
 
 @pytest.fixture(scope="module")
@@ -28,10 +36,15 @@ def _decode(form, img):
     nl = len(shifts)
     raw = np.frombuffer(img, dtype=np.uint8)
     limbs = np.zeros((nl, 64, 64))
+    zz = _zigzag()
     for l in range(nl):
         for pos in range(64):
             n = 64 * l + pos
             for kk in range(64):
+                if form == "f16":                       # row n = 64 l + zigzag index
+                    off = n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2
+                    limbs[l, zz[pos], kk] = float(raw[off:off + 2].view(np.float16)[0])
+                    continue
                 if form == "bf16":
                     off = n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2
                     bits = int(raw[off]) | int(raw[off + 1]) << 8
@@ -60,10 +73,11 @@ def test_limbs_reconstruct_the_basis(api, form):
     rem = np.abs(basis - approx)
     # each limb rounds to nearest: the remainder is at most half a unit of the last limb
     assert rem.max() <= 2.0 ** -(e + 1) * (1 + 1e-9)
-    worst = (255 * rem.sum(axis=1)).max()
+    pb = PIXEL_BOUND[form]
+    worst = (pb * rem.sum(axis=1)).max()
     assert worst <= bound < guard
     # 8-bit pixels keep every partial sum of every limb an integer below 2^24
-    assert (255 * np.abs(limbs).sum(axis=2)).max() < 2 ** 24
+    assert (pb * np.abs(limbs).sum(axis=2)).max() < 2 ** 24
 
 
 @pytest.mark.parametrize("form", sorted(FORMS))
@@ -88,13 +102,14 @@ def test_tc_host_argument_checks(api):
     from paper_1512_02951_gb300 import _lib
     lib = _lib.load()
     key = bytes(16)
-    assert lib.fds_protect_image_tc(2, 8, 64, 64, 0, key, key, 16, 16, None) == -1   # unknown form
+    assert lib.fds_protect_image_tc(3, 8, 64, 64, 0, key, key, 16, 16, None) == -1   # unknown form
     assert b"form" in lib.fds_last_error()
     assert lib.fds_protect_image_tc(0, 8, 100, 64, 0, key, key, 16, 16, None) == -1  # width
     assert lib.fds_protect_image_tc(0, 8, 64, 64, 64, key, key, 16, 16, None) == -1  # k
     assert lib.fds_protect_image_tc(1, 8, 64, 64, 0, key, key, 24, 16, None) == -1   # alignment
     assert lib.fds_debug_dct_tc(0, None, 64, 64, 16, None) == -1
     assert lib.fds_tc_basis(5, None, 0, None) == -1
+    assert lib.fds_protect_image_tc(2, 8, 64, 64, 17, key, key, 16, 16, None) == -1  # k not instantiated
     small = (ctypes.c_uint8 * 16)()
     assert lib.fds_tc_basis(0, small, 16, None) == -1
     with pytest.raises(ValueError):
