@@ -231,10 +231,12 @@ int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
 /* FDS_TC_F16 is the warp-specialised form: one persistent CTA per SM, tiles of 128 pixel
  * blocks; a producer warp moves pixel rows in with bulk copies, one thread issues the MMAs
  * (D = A B^T per channel, A = p - 128 in f16, B = the basis with rows in zigzag order split
- * as (L0 + L1 2^-11) 2^-13, |L| <= 2048, so the FP32 accumulators are exact integer sums),
- * four warps de-interleave the pixels and round the accumulators (one thread per pixel block,
- * all three channels), and four warps generate the CTR keystream ahead of use.  The error of
- * a coefficient before rounding is below the bound fds_tc_basis reports (about 3e-4); values
+ * as (L0 + L1 2^-11 + L2 2^-22) 2^-13, |L| <= 2048, so the FP32 accumulators are exact integer
+ * sums; the integer part is rounded from limb 0 alone and limbs 1, 2 only form the residual),
+ * sixteen warps de-interleave the pixels and round the accumulators (one thread per pixel
+ * block, four warps per block covering its three channels), and four warps generate the CTR keystream ahead of use.  The error of
+ * a coefficient before rounding is below the bound fds_tc_basis reports (about 6e-5, and about
+ * 1e-7 + |F| 2^-24 for a value F); values
  * within it of a half-integer are re-decided exactly.  Selections k in FDS_TC_F16_K_LIST,
  * else FDS_E_INVALID. */
 int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height,
@@ -379,8 +381,8 @@ int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]);
  * holds it in shared memory -- row n = 64 l + 8u + v is limb l of the basis function
  * (u, v), K index 8y + x, 128-byte rows, 16-byte chunk c of row n stored at chunk c ^ (n & 7);
  * the TF32 form stores K 0..31 and K 32..63 as two consecutive 128-row blocks; the F16 form
- * has rows n = 64 l + z (z the zigzag index) of limb l of 2^13 b_u(y) b_v(x) (16384 bytes).
- * out: host, at least 24576 (BF16), 32768 (TF32) or 16384 (F16) bytes, or NULL.  *error_bound (host, or NULL): the
+ * has rows n = 64 l + z (z the zigzag index) of limb l of 2^13 b_u(y) b_v(x), three limbs
+ * (24576 bytes).  out: host, at least 24576 (BF16, F16) or 32768 (TF32) bytes, or NULL.  *error_bound (host, or NULL): the
  * proven bound on |computed - exact| of a pre-rounding coefficient of 8-bit pixels. */
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound);
 

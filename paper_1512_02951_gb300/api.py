@@ -445,7 +445,7 @@ def tc_basis(form: str = "bf16") -> tuple[bytes, float]:
     """fds_tc_basis (host only): the tensor-core B operand bytes and the proven bound on the
     pre-rounding coefficient error."""
     f = _tc_form(form)
-    n = {_lib.FDS_TC_BF16: 24576, _lib.FDS_TC_TF32: 32768, _lib.FDS_TC_F16: 16384}[f]
+    n = {_lib.FDS_TC_BF16: 24576, _lib.FDS_TC_TF32: 32768, _lib.FDS_TC_F16: 24576}[f]
     buf = (ctypes.c_uint8 * n)()
     bound = ctypes.c_double()
     _lib.check(_lib.load().fds_tc_basis(f, buf, n, ctypes.byref(bound)), "fds_tc_basis")

@@ -13,7 +13,6 @@
 namespace fds {
 
 constexpr int kFullThreads = 512;
-constexpr int kTrepWords = 256 * 32;   // T0 replicated: entry x of copy L at word 32 x + L
 
 struct FullArgs {
   const uint8_t* in;
@@ -23,40 +22,6 @@ struct FullArgs {
   const uint32_t* T;
   uint32_t rk[44];
 };
-
-// AES-128 with one T-table, T0, replicated 32 times in shared memory: lane L always reads
-// copy L, i.e. bank L, so a warp's 32 lookups never conflict.  Tl = the table's byte address
-// plus 4 * lane (entry x of the lane's copy at Tl + 128 x).  T_r[x] = rotl(T0[x], 8 r) by
-// byte permutes; S[x] is byte 1 of T0[x] (last round).
-__device__ __forceinline__ void aes128_encrypt_rep(uint32_t (&s)[4], const uint32_t* rk, const char* Tl) {
-  auto l0 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w << 7) & 0x7f80u)); };
-  auto l1 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 1) & 0x7f80u)); };
-  auto l2 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 9) & 0x7f80u)); };
-  auto l3 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 17) & 0x7f80u)); };
-  auto r8 = [](uint32_t x) { return __byte_perm(x, x, 0x2103u); };
-  auto r16 = [](uint32_t x) { return __byte_perm(x, x, 0x1032u); };
-  auto r24 = [](uint32_t x) { return __byte_perm(x, x, 0x0321u); };
-  uint32_t s0 = s[0] ^ rk[0], s1 = s[1] ^ rk[1], s2 = s[2] ^ rk[2], s3 = s[3] ^ rk[3];
-#pragma unroll 1
-  for (int r = 1; r < 10; ++r) {
-    const uint32_t n0 = l0(s0) ^ r8(l1(s1)) ^ r16(l2(s2)) ^ r24(l3(s3)) ^ rk[4 * r];
-    const uint32_t n1 = l0(s1) ^ r8(l1(s2)) ^ r16(l2(s3)) ^ r24(l3(s0)) ^ rk[4 * r + 1];
-    const uint32_t n2 = l0(s2) ^ r8(l1(s3)) ^ r16(l2(s0)) ^ r24(l3(s1)) ^ rk[4 * r + 2];
-    const uint32_t n3 = l0(s3) ^ r8(l1(s0)) ^ r16(l2(s1)) ^ r24(l3(s2)) ^ rk[4 * r + 3];
-    s0 = n0;
-    s1 = n1;
-    s2 = n2;
-    s3 = n3;
-  }
-  s[0] = (__byte_perm(l0(s0), 0u, 0x4441u) | __byte_perm(l1(s1), 0u, 0x4414u) |
-          __byte_perm(l2(s2), 0u, 0x4144u) | __byte_perm(l3(s3), 0u, 0x1444u)) ^ rk[40];
-  s[1] = (__byte_perm(l0(s1), 0u, 0x4441u) | __byte_perm(l1(s2), 0u, 0x4414u) |
-          __byte_perm(l2(s3), 0u, 0x4144u) | __byte_perm(l3(s0), 0u, 0x1444u)) ^ rk[41];
-  s[2] = (__byte_perm(l0(s2), 0u, 0x4441u) | __byte_perm(l1(s3), 0u, 0x4414u) |
-          __byte_perm(l2(s0), 0u, 0x4144u) | __byte_perm(l3(s1), 0u, 0x1444u)) ^ rk[42];
-  s[3] = (__byte_perm(l0(s3), 0u, 0x4441u) | __byte_perm(l1(s0), 0u, 0x4414u) |
-          __byte_perm(l2(s1), 0u, 0x4144u) | __byte_perm(l3(s2), 0u, 0x1444u)) ^ rk[43];
-}
 
 __global__ void __launch_bounds__(kFullThreads) aes_ctr_full_kernel(const __grid_constant__ FullArgs a) {
   extern __shared__ __align__(16) uint32_t Trep[];

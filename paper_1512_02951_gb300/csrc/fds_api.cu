@@ -36,9 +36,9 @@ __device__ unsigned long long g_counters[3];
 //  g_tcb0/1   tensor-core B operands (basis limbs, BF16 / TF32) in shared-memory byte order
 __device__ __align__(16) uint4 g_tcb0[kTcBBytesBf16 / 16];
 __device__ __align__(16) uint4 g_tcb1[kTcBBytesTf32 / 16];
-//  g_mma_fwd  B operand of the warp-specialised tensor-core protect (f16, two limbs, rows in
+//  g_mma_fwd  B operand of the warp-specialised tensor-core protect (f16, three limbs, rows in
 //             zigzag order), in shared-memory byte order
-__device__ __align__(16) uint4 g_mma_fwd[16384 / 16];
+__device__ __align__(16) uint4 g_mma_fwd[kMmaFwdBytes / 16];
 
 // The exact rounding step alone: out[i] = round half away from zero of V_i, 8 V_i =
 // coords[8i] + sum_j coords[8i + j] cos(j pi/16); escalations and failures are counted like
@@ -84,7 +84,7 @@ struct DevTables {
   unsigned long long* counters;
   const uint4* tc_b[2];
   const uint4* mma_fwd;
-  float mma_fwd_guard;
+  float mma_fwd_guard, mma_fwd_guard_rem;
   int sms;
 };
 DevTables g_tables[kMaxDevices];
@@ -209,54 +209,62 @@ uint16_t f16_of_int(int v) {
   return (uint16_t)(sign | (unsigned)((e + 15) << 10) | frac);
 }
 
-// B operand of the tensor-core protect (f16, two limbs): row n = 64 l + z holds limb l of
-// 2^13 b_u(y) b_v(x) ((u, v) the zigzag position z) at K index 8y + x, split as L0 + L1 2^-11
-// with integer limbs, laid out as the kernel's 128-byte swizzled K-major shared-memory image.
-// Returns false (with a message) unless the kernel's exactness argument holds: limbs exact in
-// f16, every accumulator an integer below 2^24 for inputs |p - 128| <= 128, the rational
-// coefficients carried by limb 0 alone.  *bound: a proven bound on |computed - exact| of a
-// pre-rounding coefficient (limb remainder over |p - 128| <= 128, plus half an ulp of the one
-// rounding t = D0 + D1 2^-11 with |t| < 2^23, plus the error of cos() in double).
-bool build_mma_fwd(std::vector<uint8_t>& img, double* bound, std::string& why) {
-  img.assign(16384, 0);
+// B operand of the tensor-core protect (f16, three limbs): row n = 64 l + z holds limb l of
+// s = 2^13 b_u(y) b_v(x) ((u, v) the zigzag position z) at K index 8y + x, the split being
+// s ~ L0 + L1 2^-11 + L2 2^-22 with integer limbs, laid out as the kernel's 128-byte swizzled
+// K-major shared-memory image.  Returns false (with a message) unless the kernel's exactness
+// argument holds: limbs exact in f16, every accumulator an integer below 2^24 for inputs
+// |p - 128| <= 128, the rational coefficients carried by limb 0 alone.  The kernel forms
+// t = D1 + D2 2^-11 (|t| < 2^23: error <= 1/2) and S = D0 + t 2^-11 = 2^13 F (error <= half an
+// ulp of S, at most |S| 2^-24), then rounds S 2^-13 exactly.  *bound_rem: the limb remainder
+// over |p - 128| <= 128, plus t's rounding (2^-25 in units of F), plus the error of cos() in
+// double; the error of a value F is at most bound_rem + |F| 2^-24.  *bound: that bound for the
+// largest |F| of an irrational coefficient of 8-bit pixels.
+bool build_mma_fwd(std::vector<uint8_t>& img, double* bound, double* bound_rem, std::string& why) {
+  img.assign(kMmaFwdBytes, 0);
   double b[8][8];
   for (int u = 0; u < 8; ++u)
     for (int y = 0; y < 8; ++y) b[u][y] = (u == 0 ? std::sqrt(0.5) : 1.0) * 0.5 * std::cos((2 * y + 1) * u * std::acos(-1.0) / 16);
   int uz[64], vz[64];
   for (int u = 0; u < 8; ++u)
     for (int v = 0; v < 8; ++v) uz[zigzag_of(u, v)] = u, vz[zigzag_of(u, v)] = v;
-  double rem_max = 0, fmax = 0;
+  double rem_max = 0, tmax = 0, fmax = 0;
   for (int z = 0; z < 64; ++z) {
     const int u = uz[z], v = vz[z];
     const bool rational = (u == 0 || u == 4) && (v == 0 || v == 4);
-    double rem = 0, fsum = 0, lsum[2] = {0, 0};
+    double rem = 0, fsum = 0, lsum[3] = {0, 0, 0};
     for (int kk = 0; kk < 64; ++kk) {
       const double B = b[u][kk >> 3] * b[v][kk & 7];
       fsum += std::fabs(B);
       double r = std::ldexp(B, 13);
-      const double L0 = std::nearbyint(r);
-      r = std::ldexp(r - L0, 11);
-      const double L1 = std::nearbyint(r);
-      rem += std::ldexp(std::fabs(r - L1), -24);
-      const double L[2] = {L0, L1};
-      for (int l = 0; l < 2; ++l) {
+      double L[3];
+      for (int l = 0; l < 3; ++l) {
+        if (l) r = std::ldexp(r, 11);
+        L[l] = std::nearbyint(r);
+        r -= L[l];
+      }
+      rem += std::ldexp(std::fabs(r), -35);
+      for (int l = 0; l < 3; ++l) {
         if (std::fabs(L[l]) > 2048.0) return (why = "limb not exact in f16"), false;
         lsum[l] += std::fabs(L[l]);
         const int n = 64 * l + z;
         const uint16_t h = f16_of_int((int)L[l]);
         std::memcpy(&img[n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2], &h, 2);
       }
-      if (rational && (std::fabs(L0) != 1024.0 || L1 != 0.0))
+      if (rational && (std::fabs(L[0]) != 1024.0 || L[1] != 0.0 || L[2] != 0.0))
         return (why = "rational coefficient not carried by limb 0 alone"), false;
     }
-    for (int l = 0; l < 2; ++l)
+    for (int l = 0; l < 3; ++l)
       if (128.0 * lsum[l] >= 16777216.0) return (why = "accumulator may exceed 2^24"), false;
     rem_max = std::max(rem_max, 128.0 * rem);
+    tmax = std::max(tmax, 128.0 * (lsum[1] + std::ldexp(lsum[2], -11)));
     if (!rational) fmax = std::max(fmax, 128.0 * fsum);
   }
-  if (fmax * 8192.0 >= 8388608.0) return (why = "a coefficient may exceed 2^23 in units of 2^-13"), false;
-  *bound = rem_max + std::ldexp(1.0, -14) + 64.0 * 255.0 * std::ldexp(1.0, -50);
-  if (*bound >= 1.0 / 1024) return (why = "limb split too coarse"), false;
+  if (tmax >= 8388608.0) return (why = "the residual sum may reach 2^23"), false;
+  if (fmax * 8192.0 >= 8388608.0) return (why = "a coefficient may reach 2^23 in units of 2^-13"), false;
+  *bound_rem = rem_max + std::ldexp(1.0, -25) + 64.0 * 255.0 * std::ldexp(1.0, -50);
+  *bound = *bound_rem + std::ldexp(fmax, -24);
+  if (*bound >= std::ldexp(1.0, -12)) return (why = "limb split too coarse"), false;
   return true;
 }
 
@@ -353,16 +361,17 @@ int ensure_init(int* dev_out = nullptr) {
   }
   {
     static std::vector<uint8_t> mf;
-    static double mf_bound = 0;
+    static double mf_bound = 0, mf_rem = 0;
     static bool mf_ok = false;
     static std::string mf_why;
-    if (mf.empty()) mf_ok = build_mma_fwd(mf, &mf_bound, mf_why);
+    if (mf.empty()) mf_ok = build_mma_fwd(mf, &mf_bound, &mf_rem, mf_why);
     if (!mf_ok) return set_err(FDS_E_INVALID, "tensor-core table: " + mf_why);
     if ((e = cudaMemcpyToSymbol(g_mma_fwd, mf.data(), mf.size())) != cudaSuccess) return cuda_fail(e, "table upload");
     if ((e = cudaGetSymbolAddress(&p, g_mma_fwd)) != cudaSuccess) return cuda_fail(e, "symbol address");
     tb.mma_fwd = static_cast<const uint4*>(p);
     // the guard the kernel compares with, rounded up: float(bound) * (1 + 2^-20)
     tb.mma_fwd_guard = (float)(mf_bound * (1.0 + std::ldexp(1.0, -20)));
+    tb.mma_fwd_guard_rem = (float)(mf_rem * (1.0 + std::ldexp(1.0, -20)));
   }
   if ((e = upload_sha512_constants()) != cudaSuccess) return cuda_fail(e, "SHA-512 constants upload");
   if ((e = upload_dwt_constants()) != cudaSuccess) return cuda_fail(e, "SHA constants upload");
@@ -601,8 +610,8 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
   set_tables(a, dev);
   cudaError_t e;
   if (form == FDS_TC_F16) {
-    e = launch_protect_mma(a, g_tables[dev].mma_fwd, g_tables[dev].mma_fwd_guard, (cudaStream_t)stream, false,
-                           g_tables[dev].sms);
+    e = launch_protect_mma(a, g_tables[dev].mma_fwd, g_tables[dev].mma_fwd_guard, g_tables[dev].mma_fwd_guard_rem,
+                           (cudaStream_t)stream, false, g_tables[dev].sms);
   } else {
     a.tc_b = g_tables[dev].tc_b[form];
     e = launch_protect_tc(a, (cudaStream_t)stream, form, false, g_tables[dev].sms);
@@ -1099,7 +1108,8 @@ int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound
   std::vector<uint8_t> img;
   std::string why;
   double bound = 0;
-  const bool ok = form == FDS_TC_F16 ? build_mma_fwd(img, &bound, why) : build_tc_b(form, img, why, &bound);
+  double rem = 0;
+  const bool ok = form == FDS_TC_F16 ? build_mma_fwd(img, &bound, &rem, why) : build_tc_b(form, img, why, &bound);
   if (error_bound) *error_bound = bound;
   if (!ok) return set_err(FDS_E_INVALID, "tensor-core table: " + why);
   if (out) {
@@ -1127,8 +1137,8 @@ int fds_debug_dct_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t
   set_tables(a, dev);
   cudaError_t e;
   if (form == FDS_TC_F16) {
-    e = launch_protect_mma(a, g_tables[dev].mma_fwd, g_tables[dev].mma_fwd_guard, (cudaStream_t)stream, true,
-                           g_tables[dev].sms);
+    e = launch_protect_mma(a, g_tables[dev].mma_fwd, g_tables[dev].mma_fwd_guard, g_tables[dev].mma_fwd_guard_rem,
+                           (cudaStream_t)stream, true, g_tables[dev].sms);
   } else {
     a.tc_b = g_tables[dev].tc_b[form];
     e = launch_protect_tc(a, (cudaStream_t)stream, form, true, g_tables[dev].sms);

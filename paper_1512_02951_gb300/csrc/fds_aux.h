@@ -32,12 +32,14 @@ cudaError_t launch_dwt_restore(const uint8_t* l1, const uint8_t* l2, const uint8
 cudaError_t upload_dwt_constants();
 // bit-packed storage: packed streams -> int16 fragments, w = 11 or 8 bits per AC field
 // tensor-core protect / restore of one image (warp-specialised, tiles of 128 pixel blocks);
-// bop: the B operand image in shared-memory byte order; guard: proven bound on the error of a
-// pre-rounding value; the TileArgs fields of the image, keys and tables as for the other
+// bop: the B operand image in shared-memory byte order; the TileArgs fields of the image, keys and tables as for the other
 // kernels.  k must be one of the instantiated selections (mma_supports_k).
 struct TileArgs;
 bool mma_supports_k(int k);
-cudaError_t launch_protect_mma(const TileArgs& t, const uint4* bop, float guard, cudaStream_t s, bool debug, int sms);
+// guard: the fixed bound on the error of any pre-rounding value; guard_rem: its part that does
+// not scale with the value (the kernel adds |2^13 F| 2^-37 per value)
+cudaError_t launch_protect_mma(const TileArgs& t, const uint4* bop, float guard, float guard_rem, cudaStream_t s,
+                               bool debug, int sms);
 cudaError_t launch_unpack(const uint8_t* pub_in, const uint8_t* priv_in, int16_t* pub16, int16_t* priv16,
                           long long ncb, int k, int w, cudaStream_t s);
 }  // namespace fds

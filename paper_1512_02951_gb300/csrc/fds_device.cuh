@@ -287,6 +287,84 @@ __device__ __forceinline__ void aes128_encrypt(uint32_t (&s)[4], const uint32_t*
           __byte_perm(t0(s1 >> 16), 0u, 0x4144u) | __byte_perm(t0(s2 >> 24), 0u, 0x1444u)) ^ rk[43];
 }
 
+constexpr int kTrepWords = 256 * 32;   // T0 replicated: entry x of copy L at word 32 x + L
+
+// AES-128 with one T-table, T0, replicated 32 times in shared memory: lane L always reads
+// copy L, i.e. bank L, so a warp's 32 lookups never conflict.  Tl = the table's byte address
+// plus 4 * lane (entry x of the lane's copy at Tl + 128 x).  T_r[x] = rotl(T0[x], 8 r) by
+// byte permutes; S[x] is byte 1 of T0[x] (last round).
+__device__ __forceinline__ void aes128_encrypt_rep(uint32_t (&s)[4], const uint32_t* rk, const char* Tl) {
+  auto l0 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w << 7) & 0x7f80u)); };
+  auto l1 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 1) & 0x7f80u)); };
+  auto l2 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 9) & 0x7f80u)); };
+  auto l3 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 17) & 0x7f80u)); };
+  auto r8 = [](uint32_t x) { return __byte_perm(x, x, 0x2103u); };
+  auto r16 = [](uint32_t x) { return __byte_perm(x, x, 0x1032u); };
+  auto r24 = [](uint32_t x) { return __byte_perm(x, x, 0x0321u); };
+  uint32_t s0 = s[0] ^ rk[0], s1 = s[1] ^ rk[1], s2 = s[2] ^ rk[2], s3 = s[3] ^ rk[3];
+#pragma unroll 1
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t n0 = l0(s0) ^ r8(l1(s1)) ^ r16(l2(s2)) ^ r24(l3(s3)) ^ rk[4 * r];
+    const uint32_t n1 = l0(s1) ^ r8(l1(s2)) ^ r16(l2(s3)) ^ r24(l3(s0)) ^ rk[4 * r + 1];
+    const uint32_t n2 = l0(s2) ^ r8(l1(s3)) ^ r16(l2(s0)) ^ r24(l3(s1)) ^ rk[4 * r + 2];
+    const uint32_t n3 = l0(s3) ^ r8(l1(s0)) ^ r16(l2(s1)) ^ r24(l3(s2)) ^ rk[4 * r + 3];
+    s0 = n0;
+    s1 = n1;
+    s2 = n2;
+    s3 = n3;
+  }
+  s[0] = (__byte_perm(l0(s0), 0u, 0x4441u) | __byte_perm(l1(s1), 0u, 0x4414u) |
+          __byte_perm(l2(s2), 0u, 0x4144u) | __byte_perm(l3(s3), 0u, 0x1444u)) ^ rk[40];
+  s[1] = (__byte_perm(l0(s1), 0u, 0x4441u) | __byte_perm(l1(s2), 0u, 0x4414u) |
+          __byte_perm(l2(s3), 0u, 0x4144u) | __byte_perm(l3(s0), 0u, 0x1444u)) ^ rk[41];
+  s[2] = (__byte_perm(l0(s2), 0u, 0x4441u) | __byte_perm(l1(s3), 0u, 0x4414u) |
+          __byte_perm(l2(s0), 0u, 0x4144u) | __byte_perm(l3(s1), 0u, 0x1444u)) ^ rk[42];
+  s[3] = (__byte_perm(l0(s3), 0u, 0x4441u) | __byte_perm(l1(s0), 0u, 0x4414u) |
+          __byte_perm(l2(s1), 0u, 0x4144u) | __byte_perm(l3(s2), 0u, 0x1444u)) ^ rk[43];
+}
+
+// The same on M independent blocks at once, their rounds interleaved: the M lookups chains
+// overlap, so one warp keeps the table pipe busy where a single block per thread would wait
+// out each round's load latency.
+template <int M>
+__device__ __forceinline__ void aes128_encrypt_rep_n(uint32_t (&s)[M][4], const uint32_t* rk, const char* Tl) {
+  auto l0 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w << 7) & 0x7f80u)); };
+  auto l1 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 1) & 0x7f80u)); };
+  auto l2 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 9) & 0x7f80u)); };
+  auto l3 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tl + ((w >> 17) & 0x7f80u)); };
+  auto r8 = [](uint32_t x) { return __byte_perm(x, x, 0x2103u); };
+  auto r16 = [](uint32_t x) { return __byte_perm(x, x, 0x1032u); };
+  auto r24 = [](uint32_t x) { return __byte_perm(x, x, 0x0321u); };
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[m][c] ^= rk[c];
+#pragma unroll 1
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t k0 = rk[4 * r], k1 = rk[4 * r + 1], k2 = rk[4 * r + 2], k3 = rk[4 * r + 3];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const uint32_t s0 = s[m][0], s1 = s[m][1], s2 = s[m][2], s3 = s[m][3];
+      s[m][0] = l0(s0) ^ r8(l1(s1)) ^ r16(l2(s2)) ^ r24(l3(s3)) ^ k0;
+      s[m][1] = l0(s1) ^ r8(l1(s2)) ^ r16(l2(s3)) ^ r24(l3(s0)) ^ k1;
+      s[m][2] = l0(s2) ^ r8(l1(s3)) ^ r16(l2(s0)) ^ r24(l3(s1)) ^ k2;
+      s[m][3] = l0(s3) ^ r8(l1(s0)) ^ r16(l2(s1)) ^ r24(l3(s2)) ^ k3;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const uint32_t s0 = s[m][0], s1 = s[m][1], s2 = s[m][2], s3 = s[m][3];
+    s[m][0] = (__byte_perm(l0(s0), 0u, 0x4441u) | __byte_perm(l1(s1), 0u, 0x4414u) |
+               __byte_perm(l2(s2), 0u, 0x4144u) | __byte_perm(l3(s3), 0u, 0x1444u)) ^ rk[40];
+    s[m][1] = (__byte_perm(l0(s1), 0u, 0x4441u) | __byte_perm(l1(s2), 0u, 0x4414u) |
+               __byte_perm(l2(s3), 0u, 0x4144u) | __byte_perm(l3(s0), 0u, 0x1444u)) ^ rk[41];
+    s[m][2] = (__byte_perm(l0(s2), 0u, 0x4441u) | __byte_perm(l1(s3), 0u, 0x4414u) |
+               __byte_perm(l2(s0), 0u, 0x4144u) | __byte_perm(l3(s1), 0u, 0x1444u)) ^ rk[42];
+    s[m][3] = (__byte_perm(l0(s3), 0u, 0x4441u) | __byte_perm(l1(s0), 0u, 0x4414u) |
+               __byte_perm(l2(s1), 0u, 0x4144u) | __byte_perm(l3(s2), 0u, 0x1444u)) ^ rk[43];
+  }
+}
+
 // Counter block IV + n (128-bit big-endian addition) as four state columns.
 // iv_hi / iv_lo: the IV's bytes 0..7 / 8..15 read as big-endian integers.
 __device__ __forceinline__ void ctr_block(uint64_t iv_hi, uint64_t iv_lo, uint64_t n,

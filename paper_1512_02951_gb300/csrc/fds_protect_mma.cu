@@ -3,34 +3,41 @@
 // AES-128-CTR of the confidential fragment, one persistent CTA per SM.
 //
 // The transform as a matrix product.  For channel c of the 128 pixel blocks of a tile,
-// D[128 x 128] = A[128 x 64] B[128 x 64]^T with
+// D[128 x 192] = A[128 x 64] B[192 x 64]^T with
 //   A[b][8y + x] = p - 128 of pixel (y, x) of block b (f16, exact),
-//   B[64 l + z][8y + x] = limb l of 2^13 b_u(y) b_v(x), (u, v) the zigzag position z, split
-//     as L0 + L1 2^-11 with integer limbs |L0| <= 1970, |L1| <= 1024 (exact in f16),
+//   B[64 l + z][8y + x] = limb l of s = 2^13 b_u(y) b_v(x), (u, v) the zigzag position z,
+//     split as s ~ L0 + L1 2^-11 + L2 2^-22 with integer limbs |L0| <= 1970, |L1|, |L2| <= 1024
+//     (exact in f16),
 // so accumulator column 64 l + z of lane b is the exact integer sum over the block's 64
 // pixels of (p - 128) L_l: every product and partial sum is an integer below 2^24, whatever
-// order the tensor core adds them in.  The coefficient is F = (D0 + D1 2^-11) 2^-13; its
-// error (limb remainder + one rounding) is below a bound the host proves when it builds B;
-// values within that guard of a half-integer are re-decided exactly from integer
-// coordinates in Z[cos(pi/16)] (Sect. 6.4.3 reading: round half away from zero of the exact
-// value).  The four rational coefficients ((u, v) in {0, 4}^2, B = +-1/8) come out of limb 0
-// as exact integers 8F and are rounded in integer arithmetic.  The columns are in zigzag
-// order, so the rounded values leave in fragment order without any permutation.
+// order the tensor core adds them in.  The coefficient is F = D0 2^-13 + (D1 + D2 2^-11) 2^-24.
+// The major part D0 2^-13 is exact and is the one rounded to an integer; the residual
+// r = F - round(D0 2^-13) is formed in two roundings from the minor limbs, so that |computed
+// r - exact r| is a few 2^-25 plus the limb remainder (about 2e-7 in all; the host proves the
+// bound when it builds B).  A value with |r| within that guard of 1/2 is re-decided exactly
+// from integer coordinates in Z[cos(pi/16)] (Sect. 6.4.3 reading: round half away from zero
+// of the exact value); with a guard this small that almost never happens outside true ties.
+// The four rational coefficients ((u, v) in {0, 4}^2, B = +-1/8) come out of limb 0 as exact
+// integers 8F and are rounded in integer arithmetic.  The columns are in zigzag order, so the
+// rounded values leave in fragment order without any permutation.
 //
 // Warps (one CTA per SM, tiles of 128 consecutive pixel blocks, tile g of the image at
 // blockIdx.x + i * gridDim.x):
-//   0       producer: the tile's 8 pixel rows into a two-slot ring (bulk copies when the tile
-//           lies in one block row and is 16-byte aligned, else cp.async pieces)
-//   1       MMA: one elected thread issues 4 MMAs (K = 64) per channel into a 4-slot TMEM
-//           ring (128 columns each) and commits them to mbarriers
-//   2..9    transform, two warps per TMEM lane quadrant, one thread per pixel block (TMEM
-//           lane = block): the first warp of a pair de-interleaves pixel rows 0-3 of the
-//           block's three channels into A and rounds zigzag coefficients 0-31, the second rows
-//           4-7 and coefficients 32-63; each writes its int16 pairs to the pair's staging area
-//           in fragment layout (private words XORed with the keystream), and the pair's 32
-//           blocks of public and private fragment leave by bulk store
-//   10..13  AES: the CTR keystream of the tiles' private ranges (data-independent, so it is
-//           generated ahead into a two-slot ring), one thread per 16-byte keystream block
+//   0       control: the tiles' 8 pixel rows into a two-slot ring (bulk copies when the tile
+//           lies in one block row and is 16-byte aligned, else cp.async pieces), and, from one
+//           elected thread, 4 MMAs (K = 64) per channel into a 2-slot TMEM ring (192 columns
+//           each), committed to mbarriers
+//   1..8    epilogue, two warps per TMEM lane quadrant, one thread per pixel block (TMEM lane =
+//           block): the first rounds zigzag coefficients 0-31 of each channel, the second
+//           32-63; both write int16 pairs to the quadrant's staging area in fragment layout
+//           (private words XORed with the keystream), and the quadrant's 32 blocks of public
+//           and private fragment leave by bulk store
+//   9..12   work, one per SM sub-partition, one thread per pixel block: the block's three
+//           channels de-interleaved into A (one 16 KB operand per channel) as soon as the
+//           previous tile's MMA of the channel has read it, then a quarter of the tile's CTR
+//           keystream (AES-128, one thread per 16-byte block, T0 replicated per shared-memory
+//           bank so that a warp's table lookups never conflict) into a two-slot ring; a
+//           tile's operands and keystream are ready while the epilogue rounds the previous tile
 // Near ties are recorded (tile, block, channel, zigzag position, stored value) and decided
 // after the CTA's last tile from the image in global memory; a changed value is patched by
 // XOR (old ^ new) into the public int16 or, CTR being a stream cipher, the ciphertext.
@@ -44,25 +51,27 @@ namespace fds {
 constexpr int kPmBlocks = 128;                       // pixel blocks per tile (MMA M)
 constexpr int kPmRowBytes = kPmBlocks * 24;          // one pixel row of the tile
 constexpr int kPmPixBytes = 8 * kPmRowBytes;         // 24 KB
-constexpr int kPmTransWarps = 8;
-constexpr int kPmAesWarps = 4;
-constexpr int kPmWarps = 2 + kPmTransWarps + kPmAesWarps;
+constexpr int kPmEpiWarps = 8;                       // accumulators -> fragments, two per TMEM quadrant
+constexpr int kPmWorkWarps = 4;                      // pixels -> A operands, and the keystream
+constexpr int kPmWarps = 1 + kPmEpiWarps + kPmWorkWarps;
+constexpr int kPmPixSlots = 2;                       // pixel tiles in flight
 constexpr int kPmThreads = 32 * kPmWarps;
 constexpr int kPmStageWarp = 32 * 3 * 128;           // one quadrant's staging: 12 KB
 constexpr int kPmListCap = 512;                      // recorded near ties per CTA
-constexpr int kPmMaxK = 15;                          // largest selection this kernel takes
-constexpr int kPmTmemCols = 512;                     // 4 accumulator slots of 128 columns
+constexpr int kPmMaxK = 7;                           // largest selection this kernel takes
+constexpr int kPmN = 192;                            // accumulator columns per channel (3 limbs)
+constexpr int kPmTmemCols = 512;                     // 2 accumulator slots of 192 columns
 
 template <int K>
 struct PmSmem {
   static constexpr int kKsTile = 768 * (K + 1);      // keystream bytes of one tile
-  static constexpr int kB = 0;                       // B operand, 16 KB
-  static constexpr int kA = kB + 16384;              // A operands, 3 x 16 KB
+  static constexpr int kB = 0;                       // B operand, 24 KB
+  static constexpr int kA = kB + kMmaFwdBytes;       // A operands, 3 x 16 KB
   static constexpr int kPix = kA + 3 * 16384;        // pixel ring, 2 x 24 KB
-  static constexpr int kStage = kPix + 2 * kPmPixBytes;
+  static constexpr int kStage = kPix + kPmPixSlots * kPmPixBytes;
   static constexpr int kKs = kStage + 4 * kPmStageWarp;
-  static constexpr int kT = kKs + 2 * kKsTile;
-  static constexpr int kList = kT + 4096;
+  static constexpr int kT = kKs + 2 * kKsTile;      // AES T0 replicated per bank, 32 KB
+  static constexpr int kList = kT + 4 * kTrepWords;
   static constexpr int kBar = kList + 8 * kPmListCap;
   static constexpr int kMisc = kBar + 256;
   static constexpr int kBytes = kMisc + 64 + 1024;   // + slack for the 1024-byte alignment
@@ -71,17 +80,17 @@ static_assert(PmSmem<kPmMaxK>::kBytes <= 227 * 1024, "shared memory");
 
 // mbarriers (index into the barrier array)
 enum : int {
-  kBarPixFull = 0,     // [2] producer -> transform (32 arrivals + bytes)
-  kBarPixEmpty = 2,    // [2] transform -> producer (8)
-  kBarAFull = 4,       // [3] transform -> MMA (8)
-  kBarAEmpty = 7,      // [3] MMA commit -> transform (1)
-  kBarAccFull = 10,    // [4] MMA commit -> transform (1)
-  kBarAccEmpty = 14,   // [4] transform -> MMA (8)
-  kBarKsFull = 18,     // [2] AES -> transform (kPmAesWarps)
-  kBarKsEmpty = 20,    // [2] transform warps of coefficients 0-31 -> AES (4)
-  kBarStageFree = 22,  // [4] per quadrant: the previous tile's bulk stores have read the staging (1)
-  kBarStageFull = 26,  // [4] per quadrant: coefficients 32-63 are in the staging (1)
-  kBarCount = 30
+  kBarPixFull = 0,     // [3] producer -> work warps (32 arrivals + bytes)
+  kBarPixEmpty = 3,    // [3] work warps -> producer (kPmWorkWarps)
+  kBarAFull = 6,       // [3] work warps -> MMA (kPmWorkWarps)
+  kBarAEmpty = 9,      // [3] MMA commit -> work warps (1)
+  kBarAccFull = 12,    // [2] MMA commit -> epilogue (1)
+  kBarAccEmpty = 14,   // [2] epilogue -> MMA (kPmEpiWarps)
+  kBarKsFull = 16,     // [2] work warps -> epilogue (kPmWorkWarps)
+  kBarKsEmpty = 18,    // [2] epilogue warps of coefficients 0-31 -> work warps (4)
+  kBarStageFree = 20,  // [4] per quadrant: the previous tile's bulk stores have read the staging (1)
+  kBarStageFull = 24,  // [4] per quadrant: coefficients 32-63 are in the staging (1)
+  kBarCount = 28
 };
 // misc ints
 enum : int { kMiscList = 0, kMiscEsc = 1, kMiscFail = 2, kMiscAbort = 3, kMiscTmem = 8 };   // [0..7] zeroed at start
@@ -137,71 +146,70 @@ struct PmArgs {
   const uint4* bop;              // B operand image, 16 KB (device)
   unsigned long long* counters;  // 3 counters (device)
   int32_t width, nblocks, ntiles;
-  float guard;                   // proven bound on |computed F - exact F|
+  float guard;                   // proven bound on |computed F - exact F| (any value)
+  float guard_rem;               // the part of it that does not scale with |F|
   uint64_t iv_hi, iv_lo;
   uint32_t rk[44];
 };
 
-// One coefficient Z from its limb accumulators: the bits of F + 1.5 2^23 (their low 16 bits
-// are the int16 result), the residual r = F - round(F) (0 for the rational positions, which
-// are rounded exactly in integer arithmetic) and (DEBUG) F itself.
+// One coefficient Z from its limb accumulators d0, d1, d2: the bits of F + 1.5 2^23 (their
+// low 16 bits are the int16 result), the residual r = F - round(F) (0 for the rational
+// positions, rounded exactly in integer arithmetic) and S = 2^13 F as computed (for the
+// per-value guard and the DEBUG export).
 template <int Z>
-__device__ __forceinline__ uint32_t coef_bits(float d0, float d1, float& r, float& F) {
+__device__ __forceinline__ uint32_t coef_bits(float d0, float d1, float d2, float& r, float& S) {
   if constexpr (zz_rational(Z)) {
     const int T8 = __float2int_rn(d0 * (1.0f / 1024.0f));   // 8F (level-shifted for the DC), exact
     int q;
     if constexpr (Z == 0) {
       q = (T8 + 8192 + 4) >> 3;
-      F = (float)(T8 + 8192) * 0.125f;
+      S = (float)(T8 + 8192) * 1024.0f;
     } else {
       q = (T8 + 4 - (T8 < 0 ? 1 : 0)) >> 3;
-      F = (float)T8 * 0.125f;
+      S = (float)T8 * 1024.0f;
     }
     r = 0.0f;
     return (uint32_t)q;
   } else {
-    const float t = fmaf(d1, 1.0f / 2048.0f, d0);            // 2^13 F, one rounding
-    const float y = fmaf(t, 1.0f / 8192.0f, kMagic);          // round to nearest integer
-    r = fmaf(t, 1.0f / 8192.0f, -(y - kMagic));               // F - round(F), exact
-    F = t * (1.0f / 8192.0f);
+    const float t = fmaf(d2, 1.0f / 2048.0f, d1);             // D1 + D2 2^-11
+    S = fmaf(t, 1.0f / 2048.0f, d0);                          // 2^13 F
+    const float y = fmaf(S, 1.0f / 8192.0f, kMagic);          // round(F)
+    r = fmaf(S, 1.0f / 8192.0f, -(y - kMagic));               // F - round(F), exact
     return __float_as_uint(y);
   }
 }
 
 // the pair (Z, Z + 1), on packed f32x2 instructions when both are irrational
 template <int Z>
-__device__ __forceinline__ void coef_pair(float a0, float a1, float b0, float b1, uint32_t& qa, uint32_t& qb,
-                                          float& ra, float& rb, float& Fa, float& Fb) {
+__device__ __forceinline__ void coef_pair(float a0, float a1, float a2, float b0, float b1, float b2, uint32_t& qa,
+                                          uint32_t& qb, float& ra, float& rb, float& Sa, float& Sb) {
   if constexpr (!zz_rational(Z) && !zz_rational(Z + 1)) {
-    const float2 t = __ffma2_rn(make_float2(a1, b1), make_float2(1.0f / 2048.0f, 1.0f / 2048.0f), make_float2(a0, b0));
-    const float2 y = __ffma2_rn(t, make_float2(1.0f / 8192.0f, 1.0f / 8192.0f), make_float2(kMagic, kMagic));
+    const float2 t = __ffma2_rn(make_float2(a2, b2), make_float2(1.0f / 2048.0f, 1.0f / 2048.0f), make_float2(a1, b1));
+    const float2 S = __ffma2_rn(t, make_float2(1.0f / 2048.0f, 1.0f / 2048.0f), make_float2(a0, b0));
+    const float2 y = __ffma2_rn(S, make_float2(1.0f / 8192.0f, 1.0f / 8192.0f), make_float2(kMagic, kMagic));
     const float2 ym = __fadd2_rn(y, make_float2(-kMagic, -kMagic));
-    const float2 r = __ffma2_rn(t, make_float2(1.0f / 8192.0f, 1.0f / 8192.0f), make_float2(-ym.x, -ym.y));
+    const float2 r = __ffma2_rn(S, make_float2(1.0f / 8192.0f, 1.0f / 8192.0f), make_float2(-ym.x, -ym.y));
     qa = __float_as_uint(y.x);
     qb = __float_as_uint(y.y);
     ra = r.x;
     rb = r.y;
-    Fa = t.x * (1.0f / 8192.0f);
-    Fb = t.y * (1.0f / 8192.0f);
+    Sa = S.x;
+    Sb = S.y;
   } else {
-    qa = coef_bits<Z>(a0, a1, ra, Fa);
-    qb = coef_bits<Z + 1>(b0, b1, rb, Fb);
+    qa = coef_bits<Z>(a0, a1, a2, ra, Sa);
+    qb = coef_bits<Z + 1>(b0, b1, b2, rb, Sb);
   }
 }
 
-// The 32 coefficients z = 32 H .. 32 H + 31 of one channel-block from their limb accumulators.
-template <int H, int... P>
-__device__ __forceinline__ void round_half_seq(const uint32_t (&d0)[32], const uint32_t (&d1)[32], uint32_t (&q)[32],
-                                               float (&r)[32], float (&F)[32], std::integer_sequence<int, P...>) {
-  (coef_pair<32 * H + 2 * P>(__uint_as_float(d0[2 * P]), __uint_as_float(d1[2 * P]), __uint_as_float(d0[2 * P + 1]),
-                             __uint_as_float(d1[2 * P + 1]), q[2 * P], q[2 * P + 1], r[2 * P], r[2 * P + 1], F[2 * P],
-                             F[2 * P + 1]),
+// The 16 coefficients z = 16 P .. 16 P + 15 of one channel-block from their limb accumulators.
+template <int P, int... I>
+__device__ __forceinline__ void round_part_seq(const uint32_t (&d)[3][16], uint32_t (&q)[16], float (&r)[16],
+                                               float (&F)[16], std::integer_sequence<int, I...>) {
+  (coef_pair<16 * P + 2 * I>(__uint_as_float(d[0][2 * I]), __uint_as_float(d[1][2 * I]), __uint_as_float(d[2][2 * I]),
+                             __uint_as_float(d[0][2 * I + 1]), __uint_as_float(d[1][2 * I + 1]),
+                             __uint_as_float(d[2][2 * I + 1]), q[2 * I], q[2 * I + 1], r[2 * I], r[2 * I + 1],
+                             F[2 * I], F[2 * I + 1]),
    ...);
-}
-template <int H>
-__device__ __forceinline__ void round_half(const uint32_t (&d0)[32], const uint32_t (&d1)[32], uint32_t (&q)[32],
-                                           float (&r)[32], float (&F)[32]) {
-  round_half_seq<H>(d0, d1, q, r, F, std::make_integer_sequence<int, 16>{});
 }
 
 // Decide coefficient z of channel c of image block gb exactly, from the image in global memory.
@@ -212,14 +220,89 @@ __device__ __forceinline__ int decide_exact(const PmArgs& a, long long gb, int c
   return exact_round(n, esc, fail);
 }
 
-// Transform warp (quadrant q, coefficient half H): per tile, pixel rows 4H..4H+3 of its 32
-// blocks into the three A operands, then zigzag coefficients 32H..32H+31 of every channel from
-// the accumulators to the staging area.
+// Work warp w (one thread per pixel block 32w + lane of the tile): per tile, the block's 8
+// pixel rows from the ring into registers; per channel, as soon as the previous tile's MMA of
+// that channel has read its A slot, the block's 64 pixels of the channel as f16 (p - 128) into
+// A; then this warp's share of the tile's CTR keystream (16-byte blocks j = 32 ((w + i) mod 4)
+// + lane + 128 r, so that the warp with one round more rotates from tile to tile).
+template <int K>
+__device__ __forceinline__ void pm_work(const PmArgs& a, uint8_t* smem, uint64_t* bar, volatile int* abort, int nt,
+                                        const uint32_t* Ts) {
+  using Sm = PmSmem<K>;
+  constexpr int NB = 48 * (K + 1);            // keystream blocks of a full tile
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = warp - 1 - kPmEpiWarps;
+  const int bl = 32 * w + lane;
+  const int G = (int)gridDim.x;
+  const char* Tl = reinterpret_cast<const char*>(Ts) + 4 * lane;   // this lane's copy of T0
+  for (int i = 0; i < nt; ++i) {
+    const int s = i % kPmPixSlots;
+    if (!mbar_wait_abort(bar + kBarPixFull + s, (i / kPmPixSlots) & 1, abort)) break;
+    const uint8_t* pix = smem + Sm::kPix + s * kPmPixBytes + bl * 24;
+    uint32_t px[8][6];
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const uint2* rp = reinterpret_cast<const uint2*>(pix + y * kPmRowBytes);
+      const uint2 p01 = rp[0], p23 = rp[1], p45 = rp[2];
+      px[y][0] = p01.x, px[y][1] = p01.y, px[y][2] = p23.x, px[y][3] = p23.y, px[y][4] = p45.x, px[y][5] = p45.y;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar + kBarPixEmpty + s);       // the ring slot may be refilled
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (i >= 1 && !mbar_wait_abort(bar + kBarAEmpty + c, (i - 1) & 1, abort)) { ok = false; break; }
+      uint8_t* A = smem + Sm::kA + c * 16384;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        uint32_t lo, hi;
+        if (c == 0) {
+          lo = gather4<0>(px[y][0], px[y][1], px[y][2]);
+          hi = gather4<0>(px[y][3], px[y][4], px[y][5]);
+        } else if (c == 1) {
+          lo = gather4<1>(px[y][0], px[y][1], px[y][2]);
+          hi = gather4<1>(px[y][3], px[y][4], px[y][5]);
+        } else {
+          lo = gather4<2>(px[y][0], px[y][1], px[y][2]);
+          hi = gather4<2>(px[y][3], px[y][4], px[y][5]);
+        }
+        uint4 v;
+        bytes_to_f16x2(lo, v.x, v.y);
+        bytes_to_f16x2(hi, v.z, v.w);
+        *reinterpret_cast<uint4*>(A + sw128_offset(bl, y)) = v;
+      }
+      fence_proxy_async();                     // the A rows, for the tensor core
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar + kBarAFull + c);
+    }
+    if (!ok) break;
+    if (a.dbg) continue;                       // DEBUG: no keystream
+    // ---- keystream of tile i into slot i & 1 (free once the epilogue has used tile i - 2's)
+    const int ks = i & 1;
+    if (i >= 2 && !mbar_wait_abort(bar + kBarKsEmpty + ks, ((i >> 1) - 1) & 1, abort)) break;
+    const uint64_t first = (uint64_t)((int)blockIdx.x + i * G) * (uint64_t)NB;
+    uint8_t* kdst = smem + Sm::kKs + ks * Sm::kKsTile;
+#pragma unroll 1
+    for (int j = 32 * ((w + i) & 3) + lane; j < NB; j += 128) {
+      uint32_t st[4];
+      ctr_block(a.iv_hi, a.iv_lo, first + (uint64_t)j, st);
+      aes128_encrypt_rep(st, a.rk, Tl);
+      *reinterpret_cast<uint4*>(kdst + 16 * j) = make_uint4(st[0], st[1], st[2], st[3]);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar + kBarKsFull + ks);
+  }
+}
+
+// Epilogue warp (TMEM lane quadrant q, half H; one thread per pixel block): per tile and
+// channel, zigzag coefficients 32H .. 32H + 31 from the accumulators (two passes of 16) to the
+// quadrant's staging area, then (half 0) the quadrant's fragments out by bulk store.
 template <int K, bool DEBUG, int H>
-__device__ __forceinline__ void pm_transform(const PmArgs& a, uint8_t* smem, uint64_t* bar, int* misc,
-                                             volatile int* abort, uint2* list, uint32_t tmem, int nt) {
+__device__ __forceinline__ void pm_epilogue(const PmArgs& a, uint8_t* smem, uint64_t* bar, int* misc,
+                                            volatile int* abort, uint2* list, uint32_t tmem, int nt) {
   using Sm = PmSmem<K>;
   constexpr int kPubCb = 2 * (63 - K), kPrivCb = 2 * (K + 1);
+  static_assert(K < 32, "only half 0 reads the keystream");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;                     // TMEM lane quadrant (the warp's SM sub-partition)
   const int bl = 32 * q + lane;               // block inside the tile
@@ -227,7 +310,8 @@ __device__ __forceinline__ void pm_transform(const PmArgs& a, uint8_t* smem, uin
   uint8_t* stage = smem + Sm::kStage + q * kPmStageWarp;
   uint8_t* st_pub = stage;                    // 32 blocks x 3 x kPubCb
   uint8_t* st_priv = stage + 32 * 3 * kPubCb; // 32 blocks x 3 x kPrivCb
-  const float thr = 0.5f - a.guard;
+  const float thr = 0.5f - a.guard;          // fixed worst-case guard
+  const float thr_rel = 0.5f - a.guard_rem;  // per-value guard: plus |S| 2^-37
   const int G = (int)gridDim.x;
   int esc = 0;
   bool fail = false;
@@ -236,49 +320,6 @@ __device__ __forceinline__ void pm_transform(const PmArgs& a, uint8_t* smem, uin
     const int s = i & 1;
     const int g = (int)blockIdx.x + i * G;
     const int b0 = g * kPmBlocks, nb = min(kPmBlocks, a.nblocks - b0);
-    if (!mbar_wait_abort(bar + kBarPixFull + s, (i >> 1) & 1, abort)) break;
-    // ---- A operands: pixel rows 4H .. 4H + 3 of the three channels
-    {
-      const uint8_t* pix = smem + Sm::kPix + s * kPmPixBytes + bl * 24;
-      uint32_t w[4][6];
-#pragma unroll
-      for (int yy = 0; yy < 4; ++yy) {
-        const uint2* rp = reinterpret_cast<const uint2*>(pix + (4 * H + yy) * kPmRowBytes);
-        const uint2 p01 = rp[0], p23 = rp[1], p45 = rp[2];
-        w[yy][0] = p01.x, w[yy][1] = p01.y, w[yy][2] = p23.x, w[yy][3] = p23.y, w[yy][4] = p45.x, w[yy][5] = p45.y;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar + kBarPixEmpty + s);      // the ring slot may be refilled
-      bool ok = true;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (i >= 1 && !mbar_wait_abort(bar + kBarAEmpty + c, (i - 1) & 1, abort)) { ok = false; break; }
-        uint8_t* A = smem + Sm::kA + c * 16384;
-#pragma unroll
-        for (int yy = 0; yy < 4; ++yy) {
-          uint32_t lo, hi;
-          if (c == 0) {
-            lo = gather4<0>(w[yy][0], w[yy][1], w[yy][2]);
-            hi = gather4<0>(w[yy][3], w[yy][4], w[yy][5]);
-          } else if (c == 1) {
-            lo = gather4<1>(w[yy][0], w[yy][1], w[yy][2]);
-            hi = gather4<1>(w[yy][3], w[yy][4], w[yy][5]);
-          } else {
-            lo = gather4<2>(w[yy][0], w[yy][1], w[yy][2]);
-            hi = gather4<2>(w[yy][3], w[yy][4], w[yy][5]);
-          }
-          uint4 v;
-          bytes_to_f16x2(lo, v.x, v.y);
-          bytes_to_f16x2(hi, v.z, v.w);
-          *reinterpret_cast<uint4*>(A + sw128_offset(bl, 4 * H + yy)) = v;
-        }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar + kBarAFull + c);
-      }
-      if (!ok) break;
-    }
-    // ---- epilogue: accumulators -> int16 fragments in the staging area
     if (!DEBUG) {
       if (H == 0) {
         if (!mbar_wait_abort(bar + kBarKsFull + s, (i >> 1) & 1, abort)) break;
@@ -295,75 +336,93 @@ __device__ __forceinline__ void pm_transform(const PmArgs& a, uint8_t* smem, uin
     bool ok = true;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c, ++n) {
-      const int slot = n & 3;
-      if (!mbar_wait_abort(bar + kBarAccFull + slot, (n >> 2) & 1, abort)) { ok = false; break; }
+      const int slot = n & 1;
+      if (!mbar_wait_abort(bar + kBarAccFull + slot, (n >> 1) & 1, abort)) { ok = false; break; }
       tc_fence_after_sync();
-      uint32_t d0[32], d1[32];
-      tmem_ld32(tl + (uint32_t)(slot * 128 + 32 * H), d0);
-      tmem_ld32(tl + (uint32_t)(slot * 128 + 64 + 32 * H), d1);
-      tmem_ld_wait();
-      tc_fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar + kBarAccEmpty + slot);   // the registers hold the slot now
-      uint32_t qv[32];
-      float r[32], F[32];
-      round_half<H>(d0, d1, qv, r, F);
-      if (bl >= nb) continue;
       const long long gb = (long long)b0 + bl;               // block of the image
-      if (DEBUG) {
-        float* out = a.dbg + (uint64_t)(3 * gb + c) * 64ull;
-#pragma unroll
-        for (int i2 = 0; i2 < 32; ++i2) {
-          const int z = 32 * H + i2;
-          out[8 * zz_u(z) + zz_v(z)] = F[i2];
-        }
-        continue;
-      }
       const int cbw = 3 * lane + c;                          // channel-block inside the quadrant
       const int cbt = 3 * bl + c;                            // channel-block inside the tile
       uint16_t* pub16 = reinterpret_cast<uint16_t*>(st_pub + cbw * kPubCb);
       uint16_t* priv16 = reinterpret_cast<uint16_t*>(st_priv + cbw * kPrivCb);
       const uint16_t* kc16 = ks16 + cbt * (K + 1);
 #pragma unroll
-      for (int i2 = 0; i2 < 32; i2 += 2) {
-        const int z = 32 * H + i2;
-        if constexpr ((K & 1) == 1) {   // both fragments hold whole words per channel-block
-          const uint32_t wv = __byte_perm(qv[i2], qv[i2 + 1], 0x5410u);
-          if (z <= K)
-            *reinterpret_cast<uint32_t*>(priv16 + z) = wv ^ *reinterpret_cast<const uint32_t*>(kc16 + z);
-          else
-            *reinterpret_cast<uint32_t*>(pub16 + (z - K - 1)) = wv;
-        } else {
+      for (int pass = 0; pass < 2; ++pass) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        uint32_t d[3][16];
 #pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int ze = z + e;
-            const uint16_t v = (uint16_t)qv[i2 + e];
-            if (ze <= K)
-              priv16[ze] = v ^ kc16[ze];
+        for (int l = 0; l < 3; ++l) tmem_ld16(tl + (uint32_t)(slot * kPmN + 64 * l + 32 * H + 16 * pass), d[l]);
+        tmem_ld_wait();
+        if (pass == 1) {
+          tc_fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar + kBarAccEmpty + slot);   // the registers hold the slot now
+        }
+        uint32_t qv[16];
+        float r[16], S[16];
+        if (pass == 0)
+          round_part_seq<2 * H>(d, qv, r, S, std::make_integer_sequence<int, 8>{});
+        else
+          round_part_seq<2 * H + 1>(d, qv, r, S, std::make_integer_sequence<int, 8>{});
+        if (bl >= nb) continue;
+        const int zb = 32 * H + 16 * pass;
+        if (DEBUG) {
+          float* out = a.dbg + (uint64_t)(3 * gb + c) * 64ull;
+#pragma unroll
+          for (int i2 = 0; i2 < 16; ++i2) {
+            const int z = zb + i2;
+            out[8 * zz_u(z) + zz_v(z)] = S[i2] * (1.0f / 8192.0f);
+          }
+          continue;
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < 16; i2 += 2) {
+          const int z = zb + i2;
+          if constexpr ((K & 1) == 1) {   // both fragments hold whole words per channel-block
+            const uint32_t wv = __byte_perm(qv[i2], qv[i2 + 1], 0x5410u);
+            if (z <= K)
+              *reinterpret_cast<uint32_t*>(priv16 + z) = wv ^ *reinterpret_cast<const uint32_t*>(kc16 + z);
             else
-              pub16[ze - K - 1] = v;
+              *reinterpret_cast<uint32_t*>(pub16 + (z - K - 1)) = wv;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int ze = z + e;
+              const uint16_t v = (uint16_t)qv[i2 + e];
+              if (ze <= K)
+                priv16[ze] = v ^ kc16[ze];
+              else
+                pub16[ze - K - 1] = v;
+            }
           }
         }
-      }
-      bool near = false;
+        // near ties: |r| within the fixed worst-case guard of 1/2 first (cheap, rarely true),
+        // then with the value's own bound g_rem + |2^13 F| 2^-37 (the rounding of S is relative)
+        bool near = false;
 #pragma unroll
-      for (int i2 = 0; i2 < 32; ++i2) near = near || fabsf(r[i2]) > thr;
-      if (near) {   // rare: record the positions (or decide them now if the list is full)
-        uint32_t m = 0;
+        for (int i2 = 0; i2 < 16; ++i2) near |= fabsf(r[i2]) > thr;
+        if (near) {   // rare: record the positions (or decide them now if the list is full)
+          uint32_t m = 0;
 #pragma unroll
-        for (int i2 = 0; i2 < 32; ++i2) m |= (fabsf(r[i2]) > thr ? 1u : 0u) << i2;
-        while (m) {
-          const int i2 = __ffs(m) - 1;
-          m &= m - 1;
-          const int z = 32 * H + i2;
-          uint16_t* dst = z <= K ? priv16 + z : pub16 + (z - K - 1);
-          const uint32_t q0 = (uint32_t)(uint16_t)(*dst ^ (z <= K ? kc16[z] : (uint16_t)0));
-          const int idx = atomicAdd(&misc[kMiscList], 1);
-          if (idx < kPmListCap) {
-            list[idx] = make_uint2((uint32_t)g, (uint32_t)bl | ((uint32_t)c << 7) | ((uint32_t)z << 9) | (q0 << 16));
-          } else {
-            const int qx = decide_exact(a, gb, c, z, &esc, &fail);
-            *dst ^= (uint16_t)(q0 ^ (uint32_t)qx);
+          for (int i2 = 0; i2 < 16; ++i2) {
+            // S = 2^13 F again (the same operations as in round_part_seq)
+            const float t = fmaf(__uint_as_float(d[2][i2]), 1.0f / 2048.0f, __uint_as_float(d[1][i2]));
+            const float Sv = fmaf(t, 1.0f / 2048.0f, __uint_as_float(d[0][i2]));
+            m |= (fmaf(fabsf(Sv), 1.0f / 137438953472.0f, fabsf(r[i2])) > thr_rel ? 1u : 0u) << i2;
+          }
+          while (m) {
+            const int i2 = __ffs(m) - 1;
+            m &= m - 1;
+            const int z = zb + i2;
+            uint16_t* dst = z <= K ? priv16 + z : pub16 + (z - K - 1);
+            const uint32_t q0 = (uint32_t)(uint16_t)(*dst ^ (z <= K ? kc16[z] : (uint16_t)0));
+            const int idx = atomicAdd(&misc[kMiscList], 1);
+            if (idx < kPmListCap) {
+              list[idx] = make_uint2((uint32_t)g, (uint32_t)bl | ((uint32_t)c << 7) | ((uint32_t)z << 9) | (q0 << 16));
+            } else {
+              const int qx = decide_exact(a, gb, c, z, &esc, &fail);
+              *dst ^= (uint16_t)(q0 ^ (uint32_t)qx);
+            }
           }
         }
       }
@@ -376,8 +435,8 @@ __device__ __forceinline__ void pm_transform(const PmArgs& a, uint8_t* smem, uin
     }
     fence_proxy_async();
     __syncwarp();
-    if (H == 1) {
-      if (lane == 0) mbar_arrive(bar + kBarStageFull + q);   // coefficients 32-63 are in place
+    if (H != 0) {
+      if (lane == 0) mbar_arrive(bar + kBarStageFull + q);   // this half is in place
       continue;
     }
     if (!mbar_wait_abort(bar + kBarStageFull + q, i & 1, abort)) break;
@@ -407,7 +466,6 @@ __device__ __forceinline__ void pm_transform(const PmArgs& a, uint8_t* smem, uin
 template <int K, bool DEBUG>
 __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid_constant__ PmArgs a) {
   using Sm = PmSmem<K>;
-  constexpr int NB = 48 * (K + 1);                    // keystream blocks of a full tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sm::kBar);
@@ -423,16 +481,17 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
   const int bxc = a.width >> 3;
 
   // ---- set-up
-  for (int i = t; i < 1024; i += kPmThreads) Ts[i] = a.T[i];
-  for (int i = t; i < 1024; i += kPmThreads) reinterpret_cast<uint4*>(smem + Sm::kB)[i] = a.bop[i];
+  for (int i = t; i < kTrepWords; i += kPmThreads) Ts[i] = __ldg(a.T + (i >> 5));
+  for (int i = t; i < kMmaFwdBytes / 16; i += kPmThreads) reinterpret_cast<uint4*>(smem + Sm::kB)[i] = a.bop[i];
   if (t < 8) misc[t] = 0;
   if (t == 0) {
-    const uint32_t counts[kBarCount] = {32, 32, 8, 8, 8, 8, 8, 1, 1, 1, 1, 1, 1, 1, 8, 8, 8, 8,
-                                        kPmAesWarps, kPmAesWarps, 4, 4, 1, 1, 1, 1, 1, 1, 1, 1};
+    constexpr uint32_t W = kPmWorkWarps, E = kPmEpiWarps;
+    const uint32_t counts[kBarCount] = {32, 32, 32, W, W, W, W, W, W, 1, 1, 1, 1, 1, E, E,
+                                        W, W, 4, 4, 1, 1, 1, 1, 1, 1, 1, 1};
     for (int i = 0; i < kBarCount; ++i) mbar_init_n(bar + i, counts[i]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc<kPmTmemCols>(reinterpret_cast<uint32_t*>(misc + kMiscTmem));
+  if (warp == 0) tmem_alloc<kPmTmemCols>(reinterpret_cast<uint32_t*>(misc + kMiscTmem));
   fence_proxy_async();                                 // the B operand, for the tensor core
   tc_fence_before_sync();
   __syncthreads();
@@ -441,11 +500,9 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
   auto tile_of = [&](int i) { return (int)blockIdx.x + i * G; };
 
   if (warp == 0) {
-    // ================= producer: pixel tiles into the two-slot ring =================
-    int i = 0;
-    for (; i < nt; ++i) {
-      const int s = i & 1;
-      if (i >= 2 && !mbar_wait_abort(bar + kBarPixEmpty + s, ((i >> 1) - 1) & 1, abort)) break;
+    // ================= control: pixel tiles into the ring, MMAs =================
+    auto load_tile = [&](int i) {            // issue tile i's pixel rows into its ring slot
+      const int s = i % kPmPixSlots;
       const int g = tile_of(i);
       const int b0 = g * kPmBlocks, nb = min(kPmBlocks, a.nblocks - b0);
       uint8_t* pix = smem + Sm::kPix + s * kPmPixBytes;
@@ -468,78 +525,49 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
         }
         cp_async_arrive(bar + kBarPixFull + s);
       }
-    }
-    // copies still in flight into the ring must land before the CTA can exit
-    for (int j = max(0, i - 2); j < i; ++j) mbar_wait_abort(bar + kBarPixFull + (j & 1), (j >> 1) & 1, abort);
-  } else if (warp == 1) {
-    // ================= MMA issuer =================
-    const uint32_t idesc = idesc_f16(128, false);
+    };
+    int loaded = 0;
+    for (; loaded < nt && loaded < kPmPixSlots; ++loaded) load_tile(loaded);
+    const uint32_t idesc = idesc_f16(kPmN, false);
     const uint64_t db = sw128_kmajor_desc(smem_u32(smem + Sm::kB));
     int n = 0;
     bool ok = true;
     for (int i = 0; i < nt && ok; ++i) {
       for (int c = 0; c < 3; ++c, ++n) {
-        const int slot = n & 3;
+        const int slot = n & 1;
         if (!mbar_wait_abort(bar + kBarAFull + c, i & 1, abort)) { ok = false; break; }
-        if (n >= 4 && !mbar_wait_abort(bar + kBarAccEmpty + slot, ((n >> 2) - 1) & 1, abort)) { ok = false; break; }
+        if (n >= 2 && !mbar_wait_abort(bar + kBarAccEmpty + slot, ((n >> 1) - 1) & 1, abort)) { ok = false; break; }
         tc_fence_after_sync();
         if (lane == 0) {
           const uint64_t da = sw128_kmajor_desc(smem_u32(smem + Sm::kA + c * 16384));
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            mma_f16(tmem + (uint32_t)(slot * 128), da + 2 * ks, db + 2 * ks, idesc, ks > 0 ? 1u : 0u);
+            mma_f16(tmem + (uint32_t)(slot * kPmN), da + 2 * ks, db + 2 * ks, idesc, ks > 0 ? 1u : 0u);
           mma_commit(bar + kBarAccFull + slot);
           mma_commit(bar + kBarAEmpty + c);
         }
         __syncwarp();
       }
+      // tile i's pixels have been read by now (its A operands are complete): refill the slot
+      if (ok && loaded < nt) {
+        if (!mbar_wait_abort(bar + kBarPixEmpty + (i % kPmPixSlots), (i / kPmPixSlots) & 1, abort)) break;
+        load_tile(loaded++);
+      }
     }
-    // the last MMA must have completed before TMEM is freed
-    if (n > 0) mbar_wait_abort(bar + kBarAccFull + ((n - 1) & 3), ((n - 1) >> 2) & 1, abort);
-  } else if (warp < 2 + kPmTransWarps) {
-    // ================= transform =================
-    if (warp < 6)
-      pm_transform<K, DEBUG, 0>(a, smem, bar, misc, abort, list, tmem, nt);
+    // copies still in flight into the ring must land, and the last MMA must have completed,
+    // before the CTA can exit
+    for (int j = max(0, loaded - kPmPixSlots); j < loaded; ++j)
+      mbar_wait_abort(bar + kBarPixFull + (j % kPmPixSlots), (j / kPmPixSlots) & 1, abort);
+    if (n > 0) mbar_wait_abort(bar + kBarAccFull + ((n - 1) & 1), ((n - 1) >> 1) & 1, abort);
+  } else if (warp <= kPmEpiWarps) {
+    // ================= epilogue =================
+    if (warp <= 4)
+      pm_epilogue<K, DEBUG, 0>(a, smem, bar, misc, abort, list, tmem, nt);
     else
-      pm_transform<K, DEBUG, 1>(a, smem, bar, misc, abort, list, tmem, nt);
-  } else if (!DEBUG) {
-    // ================= AES: keystream of the private ranges, two tiles ahead =================
-    const int aw = warp - 2 - kPmTransWarps;
-    int arrived = 0, ready = 0;                 // tiles this warp has signalled / may write
-    auto make_ready = [&](int upto) {           // slots of tiles < upto are free
-      for (; ready < upto; ++ready)
-        if (ready >= 2 && !mbar_wait_abort(bar + kBarKsEmpty + (ready & 1), ((ready >> 1) - 1) & 1, abort))
-          return false;
-      return true;
-    };
-    // This warp will not touch tiles < upto again: arrive for each of them, tile by tile.  The
-    // arrival for tile t waits until tile t - 2 (same slot) was consumed, so that it counts
-    // toward tile t's phase of the barrier; it never waits for anything that needs this
-    // warp's own arrival for an earlier tile.
-    auto signal_upto = [&](int upto) {
-      for (; arrived < upto; ++arrived) {
-        if (!make_ready(arrived + 1)) return false;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar + kBarKsFull + (arrived & 1));
-      }
-      return true;
-    };
-    const long long total = (long long)nt * NB;
-    bool ok = true;
-    for (long long ch = aw; 32 * ch < total && ok; ch += kPmAesWarps) {
-      const long long v0 = 32 * ch;
-      const int tlo = (int)(v0 / NB), thi = (int)min((long long)nt - 1, (v0 + 31) / NB);
-      if (!signal_upto(tlo) || !make_ready(thi + 1)) { ok = false; break; }
-      const long long v = v0 + lane;
-      if (v < total) {
-        const int ti = (int)(v / NB), j = (int)(v - (long long)ti * NB);
-        uint32_t st[4];
-        ctr_block(a.iv_hi, a.iv_lo, (uint64_t)tile_of(ti) * NB + (uint64_t)j, st);
-        aes128_encrypt(st, a.rk, Ts);
-        *reinterpret_cast<uint4*>(smem + Sm::kKs + (ti & 1) * Sm::kKsTile + 16 * j) = make_uint4(st[0], st[1], st[2], st[3]);
-      }
-    }
-    if (ok) signal_upto(nt);
+      pm_epilogue<K, DEBUG, 1>(a, smem, bar, misc, abort, list, tmem, nt);
+  } else {
+    // ================= work: A operands and keystream =================
+    pm_work<K>(a, smem, bar, abort, nt, Ts);
   }
 
   // ================= after the tiles: near ties, counters, TMEM =================
@@ -572,7 +600,7 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
     if (misc[kMiscEsc]) atomicAdd(&a.counters[1], (unsigned long long)misc[kMiscEsc]);
     if (misc[kMiscFail] || *abort) atomicAdd(&a.counters[2], (unsigned long long)(misc[kMiscFail] + (*abort ? 1 : 0)));
   }
-  if (warp == 1) {
+  if (warp == 0) {
     tc_fence_after_sync();
     tmem_dealloc<kPmTmemCols>(tmem);
   }
@@ -589,8 +617,8 @@ static cudaError_t pm_launch_k(const PmArgs& a, cudaStream_t s, int sms) {
 }
 
 // TileArgs of one image -> the tensor-core protect; k must be 0 .. kPmMaxK
-cudaError_t launch_protect_mma(const TileArgs& t, const uint4* bop, float guard, cudaStream_t s, bool debug,
-                               int sms) {
+cudaError_t launch_protect_mma(const TileArgs& t, const uint4* bop, float guard, float guard_rem, cudaStream_t s,
+                               bool debug, int sms) {
   PmArgs a{};
   a.pixels = t.pixels_in;
   a.pub_out = t.pub_out;
@@ -604,6 +632,7 @@ cudaError_t launch_protect_mma(const TileArgs& t, const uint4* bop, float guard,
   a.nblocks = t.nblocks;
   a.ntiles = (t.nblocks + kPmBlocks - 1) / kPmBlocks;
   a.guard = guard;
+  a.guard_rem = guard_rem;
   a.iv_hi = t.iv_hi;
   a.iv_lo = t.iv_lo;
   for (int i = 0; i < 44; ++i) a.rk[i] = t.rk[i];

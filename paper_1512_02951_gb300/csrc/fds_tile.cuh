@@ -31,6 +31,7 @@ constexpr int kCtasPerSm = 2;
 // tensor-core form: bytes of the B operand (basis limbs) in shared memory
 constexpr int kTcBBytesBf16 = 192 * 128;      // 3 limbs x 64 rows x 64 bf16
 constexpr int kTcBBytesTf32 = 2 * 128 * 128;  // 2 limbs x 64 rows x 64 tf32, as two K atoms
+constexpr int kMmaFwdBytes = 192 * 128;       // warp-specialised form: 3 limbs x 64 rows x 64 f16
 
 // Forward guard.  On level-shifted pixels |p - 128| <= 128 the butterflies are within
 // 1.11e-3 of the exact coefficient (first-order bound: every rounded operation and every

@@ -12,7 +12,7 @@ from oracle import dct as odct
 
 # form -> (limb shifts, rounding guard, largest limb exact in the operand type)
 FORMS = {"bf16": ((9, 8, 8), 2.0 ** -11, 256), "tf32": ((12, 11), 2.0 ** -10, 2048),
-         "f16": ((13, 11), 2.0 ** -10, 2048)}
+         "f16": ((13, 11, 11), 2.0 ** -12, 2048)}
 # the f16 form holds its rows in zigzag order and its A operand is p - 128 (|.| <= 128)
 PIXEL_BOUND = {"bf16": 255, "tf32": 255, "f16": 128}
 
