@@ -413,8 +413,21 @@ int fds_debug_exact_round(const int32_t* coords, int32_t* out, int32_t n);
  * Host pointer to 3 uint64.  Synchronises the device.  reset != 0 clears them. */
 int fds_counters(uint64_t* out, int reset);
 
-/* Wait for all work on `stream` and report any asynchronous CUDA error. */
+/* Wait for all work on `stream` and report any asynchronous CUDA error.  Also reports the
+ * kernels' bounded waits: every wait in the library's kernels gives up after about 2 s (it
+ * never hangs), leaves the affected outputs unwritten and adds 1 to counter 2 of
+ * fds_counters; when that counter has grown since the last fds_sync (or reset) on this
+ * device, fds_sync returns FDS_E_TIMEOUT once, with the count in fds_last_error(). */
 int fds_sync(void* stream);
+
+/* The status fds_sync derives from the failure counter (host only, no device needed): FDS_OK
+ * when now <= seen, else FDS_E_TIMEOUT with a message giving now - seen. */
+int fds_status_of_failures(uint64_t seen, uint64_t now);
+
+/* Test hook: overwrite the three counters of fds_counters on the current device (host array of
+ * 3).  Synchronises the device.  Lets a test exercise fds_sync's FDS_E_TIMEOUT without
+ * making any device wait give up. */
+int fds_debug_set_counters(const uint64_t* values);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char* fds_last_error(void);

@@ -134,6 +134,8 @@ SIGNATURES = {
                                              ctypes.c_int32]),
     "fds_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "fds_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "fds_status_of_failures": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64]),
+    "fds_debug_set_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "fds_last_error": (ctypes.c_char_p, []),
 }
 

@@ -484,6 +484,12 @@ def counters(reset: bool = False) -> tuple[int, int, int]:
     return int(out[0]), int(out[1]), int(out[2])
 
 
+def debug_set_counters(values) -> None:
+    """fds_debug_set_counters: overwrite the three device counters (a test hook)."""
+    arr = (ctypes.c_uint64 * 3)(*[int(v) for v in values])
+    _lib.check(_lib.load().fds_debug_set_counters(arr), "fds_debug_set_counters")
+
+
 def sync() -> None:
     """fds_sync on the current stream."""
     _lib.check(_lib.load().fds_sync(_stream_ptr(torch.device("cuda"))), "fds_sync")

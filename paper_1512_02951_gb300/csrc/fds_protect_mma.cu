@@ -59,8 +59,9 @@ constexpr int kPmThreads = 32 * kPmWarps;
 constexpr int kPmStageWarp = 32 * 3 * 128;           // one quadrant's staging: 12 KB
 constexpr int kPmListCap = 512;                      // recorded near ties per CTA
 constexpr int kPmMaxK = 7;                           // largest selection this kernel takes
-constexpr int kPmN = 192;                            // accumulator columns per channel (3 limbs)
-constexpr int kPmTmemCols = 512;                     // 2 accumulator slots of 192 columns
+constexpr int kPmN = 64 * kMmaFwdLimbs;              // accumulator columns per channel
+constexpr int kPmTmemCols = 512;
+constexpr int kPmAccSlots = kPmTmemCols / kPmN >= 4 ? 4 : 2;   // accumulator slots (a ring)
 
 template <int K>
 struct PmSmem {
@@ -84,13 +85,13 @@ enum : int {
   kBarPixEmpty = 3,    // [3] work warps -> producer (kPmWorkWarps)
   kBarAFull = 6,       // [3] work warps -> MMA (kPmWorkWarps)
   kBarAEmpty = 9,      // [3] MMA commit -> work warps (1)
-  kBarAccFull = 12,    // [2] MMA commit -> epilogue (1)
-  kBarAccEmpty = 14,   // [2] epilogue -> MMA (kPmEpiWarps)
-  kBarKsFull = 16,     // [2] work warps -> epilogue (kPmWorkWarps)
-  kBarKsEmpty = 18,    // [2] epilogue warps of coefficients 0-31 -> work warps (4)
-  kBarStageFree = 20,  // [4] per quadrant: the previous tile's bulk stores have read the staging (1)
-  kBarStageFull = 24,  // [4] per quadrant: coefficients 32-63 are in the staging (1)
-  kBarCount = 28
+  kBarAccFull = 12,    // [kPmAccSlots] MMA commit -> epilogue (1)
+  kBarAccEmpty = 16,   // [kPmAccSlots] epilogue -> MMA (kPmEpiWarps)
+  kBarKsFull = 20,     // [2] work warps -> epilogue (kPmWorkWarps)
+  kBarKsEmpty = 22,    // [2] epilogue warps of coefficients 0-31 -> work warps (4)
+  kBarStageFree = 24,  // [4] per quadrant: the previous tile's bulk stores have read the staging (1)
+  kBarStageFull = 28,  // [4] per quadrant: coefficients 32-63 are in the staging (1)
+  kBarCount = 32
 };
 // misc ints
 enum : int { kMiscList = 0, kMiscEsc = 1, kMiscFail = 2, kMiscAbort = 3, kMiscTmem = 8 };   // [0..7] zeroed at start
@@ -171,7 +172,7 @@ __device__ __forceinline__ uint32_t coef_bits(float d0, float d1, float d2, floa
     r = 0.0f;
     return (uint32_t)q;
   } else {
-    const float t = fmaf(d2, 1.0f / 2048.0f, d1);             // D1 + D2 2^-11
+    const float t = kMmaFwdLimbs == 3 ? fmaf(d2, 1.0f / 2048.0f, d1) : d1;   // D1 + D2 2^-11
     S = fmaf(t, 1.0f / 2048.0f, d0);                          // 2^13 F
     const float y = fmaf(S, 1.0f / 8192.0f, kMagic);          // round(F)
     r = fmaf(S, 1.0f / 8192.0f, -(y - kMagic));               // F - round(F), exact
@@ -184,7 +185,9 @@ template <int Z>
 __device__ __forceinline__ void coef_pair(float a0, float a1, float a2, float b0, float b1, float b2, uint32_t& qa,
                                           uint32_t& qb, float& ra, float& rb, float& Sa, float& Sb) {
   if constexpr (!zz_rational(Z) && !zz_rational(Z + 1)) {
-    const float2 t = __ffma2_rn(make_float2(a2, b2), make_float2(1.0f / 2048.0f, 1.0f / 2048.0f), make_float2(a1, b1));
+    const float2 t = kMmaFwdLimbs == 3
+                         ? __ffma2_rn(make_float2(a2, b2), make_float2(1.0f / 2048.0f, 1.0f / 2048.0f), make_float2(a1, b1))
+                         : make_float2(a1, b1);
     const float2 S = __ffma2_rn(t, make_float2(1.0f / 2048.0f, 1.0f / 2048.0f), make_float2(a0, b0));
     const float2 y = __ffma2_rn(S, make_float2(1.0f / 8192.0f, 1.0f / 8192.0f), make_float2(kMagic, kMagic));
     const float2 ym = __fadd2_rn(y, make_float2(-kMagic, -kMagic));
@@ -336,8 +339,8 @@ __device__ __forceinline__ void pm_epilogue(const PmArgs& a, uint8_t* smem, uint
     bool ok = true;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c, ++n) {
-      const int slot = n & 1;
-      if (!mbar_wait_abort(bar + kBarAccFull + slot, (n >> 1) & 1, abort)) { ok = false; break; }
+      const int slot = n % kPmAccSlots;
+      if (!mbar_wait_abort(bar + kBarAccFull + slot, (n / kPmAccSlots) & 1, abort)) { ok = false; break; }
       tc_fence_after_sync();
       const long long gb = (long long)b0 + bl;               // block of the image
       const int cbw = 3 * lane + c;                          // channel-block inside the quadrant
@@ -351,7 +354,11 @@ __device__ __forceinline__ void pm_epilogue(const PmArgs& a, uint8_t* smem, uint
         (void)dummy;
         uint32_t d[3][16];
 #pragma unroll
-        for (int l = 0; l < 3; ++l) tmem_ld16(tl + (uint32_t)(slot * kPmN + 64 * l + 32 * H + 16 * pass), d[l]);
+        for (int l = 0; l < kMmaFwdLimbs; ++l) tmem_ld16(tl + (uint32_t)(slot * kPmN + 64 * l + 32 * H + 16 * pass), d[l]);
+#pragma unroll
+        for (int l = kMmaFwdLimbs; l < 3; ++l)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[l][j] = 0u;
         tmem_ld_wait();
         if (pass == 1) {
           tc_fence_before_sync();
@@ -406,7 +413,8 @@ __device__ __forceinline__ void pm_epilogue(const PmArgs& a, uint8_t* smem, uint
 #pragma unroll
           for (int i2 = 0; i2 < 16; ++i2) {
             // S = 2^13 F again (the same operations as in round_part_seq)
-            const float t = fmaf(__uint_as_float(d[2][i2]), 1.0f / 2048.0f, __uint_as_float(d[1][i2]));
+            const float t = kMmaFwdLimbs == 3 ? fmaf(__uint_as_float(d[2][i2]), 1.0f / 2048.0f, __uint_as_float(d[1][i2]))
+                                              : __uint_as_float(d[1][i2]);
             const float Sv = fmaf(t, 1.0f / 2048.0f, __uint_as_float(d[0][i2]));
             m |= (fmaf(fabsf(Sv), 1.0f / 137438953472.0f, fabsf(r[i2])) > thr_rel ? 1u : 0u) << i2;
           }
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
   if (t < 8) misc[t] = 0;
   if (t == 0) {
     constexpr uint32_t W = kPmWorkWarps, E = kPmEpiWarps;
-    const uint32_t counts[kBarCount] = {32, 32, 32, W, W, W, W, W, W, 1, 1, 1, 1, 1, E, E,
+    const uint32_t counts[kBarCount] = {32, 32, 32, W, W, W, W, W, W, 1, 1, 1, 1, 1, 1, 1, E, E, E, E,
                                         W, W, 4, 4, 1, 1, 1, 1, 1, 1, 1, 1};
     for (int i = 0; i < kBarCount; ++i) mbar_init_n(bar + i, counts[i]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -534,9 +542,12 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
     bool ok = true;
     for (int i = 0; i < nt && ok; ++i) {
       for (int c = 0; c < 3; ++c, ++n) {
-        const int slot = n & 1;
+        const int slot = n % kPmAccSlots;
         if (!mbar_wait_abort(bar + kBarAFull + c, i & 1, abort)) { ok = false; break; }
-        if (n >= 2 && !mbar_wait_abort(bar + kBarAccEmpty + slot, ((n >> 1) - 1) & 1, abort)) { ok = false; break; }
+        if (n >= kPmAccSlots && !mbar_wait_abort(bar + kBarAccEmpty + slot, ((n / kPmAccSlots) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
         tc_fence_after_sync();
         if (lane == 0) {
           const uint64_t da = sw128_kmajor_desc(smem_u32(smem + Sm::kA + c * 16384));
@@ -558,7 +569,7 @@ __global__ void __launch_bounds__(kPmThreads, 1) protect_mma_kernel(const __grid
     // before the CTA can exit
     for (int j = max(0, loaded - kPmPixSlots); j < loaded; ++j)
       mbar_wait_abort(bar + kBarPixFull + (j % kPmPixSlots), (j / kPmPixSlots) & 1, abort);
-    if (n > 0) mbar_wait_abort(bar + kBarAccFull + ((n - 1) & 1), ((n - 1) >> 1) & 1, abort);
+    if (n > 0) mbar_wait_abort(bar + kBarAccFull + ((n - 1) % kPmAccSlots), ((n - 1) / kPmAccSlots) & 1, abort);
   } else if (warp <= kPmEpiWarps) {
     // ================= epilogue =================
     if (warp <= 4)

@@ -298,6 +298,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
   }
   int esc = 0;
   bool fail = false;
+  // a fragment load that did not complete in time leaves its tile's pixels unwritten (the
+  // failure counter records it): cur_lost for the tile being transformed, lost counts them all
+  int cur_lost = lost;
   for (int it = 0;; ++it) {
     const int buf = it & 1;
     const int cur = misc[4 + buf], nxt = misc[4 + (buf ^ 1)];
@@ -399,6 +402,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         }
       }
     }
+    const int lost_before_next = lost;
     if (nxt < ntiles) {
       if constexpr (PACK != 0)
         wait_packed<PACK>(slot((it + 1) % 3), bars + (buf ^ 1), phase[buf ^ 1], lost);
@@ -433,8 +437,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
       decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
     }
     fence_proxy_async();                                  // pixel writes before the bulk stores
-    __syncthreads();                                                       // C
-    {
+    const bool skip = __syncthreads_or(cur_lost != 0);                     // C
+    cur_lost = lost - lost_before_next;                   // the next tile's fragments
+    if (skip) {
+      if (t == 0) bulk_commit();                 // an empty group keeps one group per tile
+    } else {
       // the pixel tile to global memory: one bulk (TMA engine) store per pixel row when the
       // tile's blocks are contiguous and 16-byte aligned in every row, else 8-byte stores
       const uint64_t w3 = (uint64_t)sl->width * 3ull;

@@ -31,7 +31,12 @@ constexpr int kCtasPerSm = 2;
 // tensor-core form: bytes of the B operand (basis limbs) in shared memory
 constexpr int kTcBBytesBf16 = 192 * 128;      // 3 limbs x 64 rows x 64 bf16
 constexpr int kTcBBytesTf32 = 2 * 128 * 128;  // 2 limbs x 64 rows x 64 tf32, as two K atoms
-constexpr int kMmaFwdBytes = 192 * 128;       // warp-specialised form: 3 limbs x 64 rows x 64 f16
+// warp-specialised form: FDS_MMA_LIMBS f16 limbs of the basis (2 or 3) x 64 rows x 64 f16
+#ifndef FDS_MMA_LIMBS
+#define FDS_MMA_LIMBS 3
+#endif
+constexpr int kMmaFwdLimbs = FDS_MMA_LIMBS;
+constexpr int kMmaFwdBytes = kMmaFwdLimbs * 64 * 128;
 
 // Forward guard.  On level-shifted pixels |p - 128| <= 128 the butterflies are within
 // 1.11e-3 of the exact coefficient (first-order bound: every rounded operation and every

@@ -214,3 +214,15 @@ def test_exact_round_diagnostic_rejects_vectors_outside_the_proven_range(lib):
     bad2 = (ctypes.c_int32 * 8)(0, 1 << 25, -(1 << 25), 0, 0, 0, 0, 0)
     assert lib.fds_debug_exact_round(bad2, out, 1) == -1
     assert lib.fds_debug_exact_round(None, None, -1) == -1
+
+
+def test_failure_counter_maps_to_timeout_status(lib):
+    # fds_sync reports bounded device waits that gave up: the mapping from a counter reading
+    assert lib.fds_status_of_failures(0, 0) == 0
+    assert lib.fds_status_of_failures(3, 3) == 0
+    assert lib.fds_status_of_failures(5, 2) == 0
+    assert lib.fds_status_of_failures(0, 1) == -5
+    assert b"1 bounded device wait" in lib.fds_last_error()
+    assert lib.fds_status_of_failures(7, 10) == -5
+    assert lib.fds_last_error().startswith(b"3 ")
+    assert lib.fds_debug_set_counters(None) == -1
