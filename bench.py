@@ -255,26 +255,40 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 self.out, _ = self.proc.communicate()
+        ClockSampler.log.append(self.out or "")
+
+    log: list = []      # samples of every timed region of this process, for emit()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        for ln in (self.out or "").splitlines():
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 8:
-                continue
-            try:
-                sm.append(float(f[0]))
-                mx = float(f[1])
-            except ValueError:
-                continue
-            for name, val in zip(self.NAMES, f[4:8]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return clock_summary(self.out)
+
+
+def clock_summary(text):
+    """Median SM clock, max clock and active throttle reasons of nvidia-smi samples."""
+    sm, mx, reasons = [], None, set()
+    for ln in (text or "").splitlines():
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 8:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx = float(f[1])
+        except ValueError:
+            continue
+        for name, val in zip(ClockSampler.NAMES, f[4:8]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def emit(line):
+    """Print a secondary workload's JSON line with the clocks sampled during its timed regions."""
+    line.setdefault("clocks", clock_summary("\n".join(ClockSampler.log)))
+    print(json.dumps(line), flush=True)
 
 
 def gpu_arm(args):
@@ -487,12 +501,13 @@ def batch_arm(args):
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 fn()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                fn()
-            e1.record(stream)
-        torch.cuda.synchronize()
+            with ClockSampler(0):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
     per_image = timed(lambda: (api.protect(px, pub, priv, descs), api.restore(pub, priv, out, descs)),
@@ -500,31 +515,44 @@ def batch_arm(args):
     ref = (pub.cpu().numpy().copy(), priv.cpu().numpy().copy(), out.cpu().numpy().copy())
     plan = api.Plan(descs)
     with torch.cuda.stream(stream):
-        sched = plan.autotune(px, pub, priv, reps=3)
+        fixed = {}
+        for name, ps in (("default_residency", 0), ("one_cta_per_sm", 1)):
+            plan.set_schedule(ps, False, False)
+            fixed[name] = timed(lambda: (plan.protect(px, pub, priv), plan.restore(pub, priv, out)), args.steps)
+        tuned = plan.tune(px, pub, priv, out, reps=3)
     plain = timed(lambda: (plan.protect(px, pub, priv), plan.restore(pub, priv, out)), args.steps)
     graphed = timed(lambda: (plan.protect(px, pub, priv, graph=True),
                              plan.restore(pub, priv, out, graph=True)), args.steps)
     got = (pub.cpu().numpy(), priv.cpu().numpy(), out.cpu().numpy())
     same = all(np.array_equal(a, b) for a, b in zip(ref, got))
-    with torch.cuda.stream(stream):
-        prot = timed(lambda: plan.protect(px, pub, priv, graph=True), args.steps)
+    prot = timed(lambda: plan.protect(px, pub, priv, graph=True), args.steps)
+    rest = timed(lambda: plan.restore(pub, priv, out, graph=True), args.steps)
+    cands = tuned["candidates"]
+    sched = {"size_class": tuned["size_class"], "largest_first": tuned["largest_first"],
+             "protect": tuned["protect"], "restore": tuned["restore"], "candidates_timed": len(cands),
+             "candidate_ms_range": {d: [round(min(c["ms"] for c in cands if c["direction"] == d), 4),
+                                        round(max(c["ms"] for c in cands if c["direction"] == d), 4)]
+                                    for d in ("protect", "restore")}}
     line = {"metric": METRIC + " (batched form)", "value": round(pix_bytes / (graphed * 1e-3) / 1e6, 1),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(graphed, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{BATCH_N} RGB uint8 images, W,H log-uniform [64,2048], k={BATCH_K}, "
                                    "protect+restore", "images": BATCH_N, "pixel_bytes": pix_bytes,
-                       "schedule": {"ctas_per_sm": sched[0], "dynamic": sched[1], "largest_first": sched[2]}},
+                       "schedule": sched},
             "images_per_s": {"graph": round(BATCH_N / (graphed * 1e-3), 1),
                              "plan_no_graph": round(BATCH_N / (plain * 1e-3), 1),
                              "per_image_launches": round(BATCH_N / (per_image * 1e-3), 1)},
             "ms": {"graph": round(graphed, 4), "plan_no_graph": round(plain, 4),
-                   "per_image_launches": round(per_image, 4), "protect_graph": round(prot, 4)},
+                   "per_image_launches": round(per_image, 4), "protect_graph": round(prot, 4),
+                   "restore_graph": round(rest, 4),
+                   "untuned_plan": {k: round(v, 4) for k, v in fixed.items()}},
             "bit_identical_to_per_image": same,
             "protect_roofline_frac": round(pix_bytes * 3 / (prot * 1e-3) / 1e9 / _peaks()[0], 4),
+            "restore_roofline_frac": round(pix_bytes * 3 / (rest * 1e-3) / 1e9 / _peaks()[0], 4),
             "gpu_launches": 2 * args.steps}
     plan.close()
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 # ------------------------------------------------------------------------------------------
@@ -544,6 +572,27 @@ def _fp64_dct(img):
     h, w, _ = img.shape
     blk = img.to(torch.float64).reshape(h // 8, 8, w // 8, 8, 3).permute(0, 2, 4, 1, 3)
     return torch.einsum("uy,abcyx,vx->abcuv", b, blk, b)
+
+
+def _median_launch_ms(fn, args, flush, stream):
+    """Median CUDA-event time of args.steps launches of fn after args.warmup, L2 flushed
+    between them, nvidia-smi clocks sampled meanwhile."""
+    import numpy as np
+    import torch
+
+    for _ in range(args.warmup):
+        fn()
+    ts = []
+    with ClockSampler(0):
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
 
 
 def precision_arm(args):
@@ -570,7 +619,10 @@ def precision_arm(args):
              "bf16_3limb_tcgen05": (lambda: api.protect_image_tc(img, key, iv, K_SEL, "bf16", pub, priv),
                                     lambda: api.debug_dct_tc(img, "bf16")),
              "tf32_2limb_tcgen05": (lambda: api.protect_image_tc(img, key, iv, K_SEL, "tf32", pub, priv),
-                                    lambda: api.debug_dct_tc(img, "tf32"))}
+                                    lambda: api.debug_dct_tc(img, "tf32")),
+             "f16_3limb_tcgen05_warp_specialised": (
+                 lambda: api.protect_image_tc(img, key, iv, K_SEL, "f16", pub, priv),
+                 lambda: api.debug_dct_tc(img, "f16"))}
     alg_bytes = WIDTH * HEIGHT * 3 + pub_b + priv_b
     peak, _ = _peaks()
     res, first = {}, None
@@ -585,25 +637,23 @@ def precision_arm(args):
             first = frags
         api.restore_image(pub, priv, WIDTH, HEIGHT, K_SEL, key, iv, out)
         exact_frac = (out == img).to(torch.float64).mean().item()
-        for _ in range(args.warmup):
-            protect()
-        ts = []
-        for _ in range(args.steps):
-            flush.fill_(1)                                  # L2 flushed between timed launches
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            protect()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        ms = float(np.median(ts))
+        ms = _median_launch_ms(protect, args, flush, stream)
         gbs = alg_bytes / (ms * 1e-3) / 1e9
         res[name] = {"protect_ms": round(ms, 5), "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
                      "max_abs_coef_err_vs_fp64": err, "slow_path_values": slow, "escalations_256bit": esc,
                      "failures": fails, "exact_restore_fraction": round(exact_frac, 6),
                      "bit_identical_to_f32_path": bool(torch.equal(frags[0], first[0]) and
                                                        torch.equal(frags[1], first[1]))}
-    bounds = {f: api.tc_basis(f)[1] for f in ("bf16", "tf32")}
+    api.protect_image(img, key, iv, K_SEL, pub, priv)
+    rms = _median_launch_ms(lambda: api.restore_image(pub, priv, WIDTH, HEIGHT, K_SEL, key, iv, out),
+                            args, flush, stream)
+    rgbs = alg_bytes / (rms * 1e-3) / 1e9
+    restore = {"f32_cuda_cores": {"restore_ms": round(rms, 5), "achieved_gbs": round(rgbs, 1),
+                                  "frac": round(rgbs / peak, 4)},
+               "tensor_core_inverse": "not built: the inverse transform stays on the float32 CUDA cores "
+                                      "(exact by the same guard); the forward tensor-core forms are slower "
+                                      "than the float32 kernel, so an inverse one would not pay"}
+    bounds = {f: api.tc_basis(f)[1] for f in ("bf16", "tf32", "f16")}
     best = max(res.values(), key=lambda r: r["achieved_gbs"])
     line = {"metric": "protect MB/s of pixels (precision forms)",
             "value": round(WIDTH * HEIGHT * 3 / (res["bf16_3limb_tcgen05"]["protect_ms"] * 1e-3) / 1e6, 1),
@@ -613,11 +663,11 @@ def precision_arm(args):
             "data": "synthetic",
             "config": {"workload": f"{WIDTH}x{HEIGHT} RGB uint8, protect, k={K_SEL}, DCT as tensor-core MMAs",
                        "l2": "256 MB buffer written between timed launches"},
-            "forms": res, "proven_error_bounds": bounds,
+            "forms": res, "restore": restore, "proven_error_bounds": bounds,
             "roofline": {"bound": "hbm", "achieved": best["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": best["frac"], "traffic": None},
-            "gpu_launches": args.steps * len(forms)}
-    print(json.dumps(line), flush=True)
+            "gpu_launches": args.steps * (len(forms) + 1)}
+    emit(line)
 
 
 # ------------------------------------------------------------------------------------------
@@ -640,18 +690,7 @@ def compare_arm(args):
     full_out = torch.empty_like(img)
 
     def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        ts = []
-        for _ in range(args.steps):
-            flush.fill_(1)                                  # L2 flushed between timed launches
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
+        return _median_launch_ms(fn, args, flush, stream)   # L2 flushed between timed launches
 
     res = {}
     full_ms = timed(lambda: api.encrypt_full(img, key, iv, out=full_out))
@@ -680,7 +719,7 @@ def compare_arm(args):
             "full_encryption_roofline": {"bound": "hbm", "achieved": round(full_gbs, 1), "peak": peak,
                                          "unit": "GB/s", "frac": round(full_gbs / peak, 4)},
             "gpu_launches": args.steps * 5}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 # ------------------------------------------------------------------------------------------
@@ -703,18 +742,7 @@ def packed_arm(args):
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        ts = []
-        for _ in range(args.steps):
-            flush.fill_(1)                                  # L2 flushed between timed launches
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
+        return _median_launch_ms(fn, args, flush, stream)   # L2 flushed between timed launches
 
     res = {}
     pub16_b, priv16_b = api.sizes(WIDTH, HEIGHT, K_SEL)
@@ -751,7 +779,7 @@ def packed_arm(args):
                                    "fragment storage", "l2": "256 MB buffer written between timed launches"},
             "results": res,
             "gpu_launches": args.steps * 6}   # int16 2 + 2 forms x (protect 1 + restore 1)
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 # ------------------------------------------------------------------------------------------
@@ -775,18 +803,7 @@ def strong_arm(args):
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        ts = []
-        for _ in range(args.steps):
-            flush.fill_(1)                                  # L2 flushed between timed launches
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
+        return _median_launch_ms(fn, args, flush, stream)   # L2 flushed between timed launches
 
     _, priv_b, scr_b = api.sizes_strong(WIDTH, HEIGHT, K_SEL)
     scratch = torch.empty(scr_b, dtype=torch.uint8, device=dev)
@@ -831,7 +848,7 @@ def strong_arm(args):
                        "l2": "256 MB buffer written between timed launches"},
             "results": res,
             "gpu_launches": args.steps * (4 + 4 + 1 + 1 + 1)}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 # ------------------------------------------------------------------------------------------
@@ -857,18 +874,7 @@ def dwt_arm(args):
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        ts = []
-        for _ in range(args.steps):
-            flush.fill_(1)                                  # L2 flushed between timed launches
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
+        return _median_launch_ms(fn, args, flush, stream)   # L2 flushed between timed launches
 
     outs = tuple(torch.empty(n, dtype=torch.uint8, device=dev) for n in api.dwt_sizes(DWT_W, DWT_H))
     back = torch.empty_like(data)
@@ -897,7 +903,7 @@ def dwt_arm(args):
                        "l2": "256 MB buffer written between timed launches"},
             "results": res,
             "gpu_launches": args.steps * 3}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 # ------------------------------------------------------------------------------------------
@@ -942,11 +948,13 @@ def serve_arm(args):
     warm = [Request(r.kind, r.width, r.height, r.k, r.key_slot, r.iv, r.pixels, r.public, r.private)
             for r in reqs]
     run_poisson(srv, warm, np.zeros(len(warm)))
-    poisson = run_poisson(srv, reqs, arrivals)
+    with ClockSampler(0):
+        poisson = run_poisson(srv, reqs, arrivals)
     stats_p = dict(srv.stats)
     again = [Request(r.kind, r.width, r.height, r.k, r.key_slot, r.iv, r.pixels, r.public, r.private)
              for r in reqs]
-    burst = run_poisson(srv, again, np.zeros(len(again)))      # all at once: saturation
+    with ClockSampler(0):
+        burst = run_poisson(srv, again, np.zeros(len(again)))      # all at once: saturation
     srv.close()
     same = all((np.array_equal(a.future.result()[0], b.future.result()[0]) and
                 a.future.result()[1] == b.future.result()[1]) if a.kind == "protect"
@@ -963,7 +971,7 @@ def serve_arm(args):
             "batches": stats_p["batches"], "max_batch": stats_p["max_batch"],
             "max_lanes_busy": stats_p["max_lanes_busy"],
             "same_results_in_both_runs": same}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def main():

@@ -138,21 +138,58 @@ int fds_plan_reserve(int32_t capacity, fds_plan** plan_out);
  * after it).  Waits only for the previous update's copy to have left the staging area. */
 int fds_plan_update(fds_plan* plan, const fds_image* images, int32_t n, void* stream);
 
-/* Schedule of the persistent launch.  ctas_per_sm: 1 or 2 resident CTAs per SM;
- * dynamic: 0 = static round-robin tile assignment, 1 = tiles handed out by an atomic
- * counter; largest_first: 0 = tiles in descriptor order, 1 = images by decreasing size.
- * Re-uploads the schedule and drops captured graphs. */
+/* Resident CTAs per SM of the two persistent kernels: the most a schedule may launch. */
+#define FDS_PROTECT_MAX_CTAS_PER_SM 4
+#define FDS_RESTORE_MAX_CTAS_PER_SM 2
+
+/* Schedule of the persistent launches, both directions at once.  ctas_per_sm: CTAs per SM
+ * to launch, 0 = the kernel's residency (protect 4, restore 2), 1 .. 4 (restore takes
+ * values above 2 as 0); dynamic: 0 = static round-robin tile assignment, 1 = tiles handed
+ * out by an atomic counter; largest_first: 0 = tiles in descriptor order, 1 = images by
+ * decreasing size (shared by the directions).  The lane schedule of both directions goes
+ * back to one keystream block per thread.  Re-uploads the tile order when it changes and
+ * drops captured graphs.  FDS_E_INVALID for ctas_per_sm outside 0 .. 4. */
 int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic,
                           int32_t largest_first);
 
-/* Read the current schedule (host pointers, each may be NULL). */
+/* Read the schedule (the protect direction's ctas_per_sm and dynamic; host pointers, each
+ * may be NULL). */
 int fds_plan_get_schedule(const fds_plan* plan, int32_t* ctas_per_sm, int32_t* dynamic,
                           int32_t* largest_first);
 
-/* Time every schedule on this batch (protect, `reps` launches each, on `stream`) and keep
- * the fastest.  The buffers are written to; their previous contents are lost. */
+/* Schedule of one direction (0 = protect, 1 = restore): ctas_per_sm 0 .. the direction's
+ * FDS_*_MAX_CTAS_PER_SM, dynamic as above, aes_pair: 0 = each thread of a CTA encrypts one
+ * 16-byte keystream block of the tile at a time, 1 = two blocks with their AES rounds
+ * interleaved (fewer threads, more independent lookups each; it pays only where a tile has
+ * more keystream blocks than a CTA has threads, k > 7).  Drops captured graphs.
+ * FDS_E_INVALID for a bad direction or value. */
+int fds_plan_set_direction_schedule(fds_plan* plan, int32_t direction, int32_t ctas_per_sm,
+                                    int32_t dynamic, int32_t aes_pair);
+int fds_plan_get_direction_schedule(const fds_plan* plan, int32_t direction,
+                                    int32_t* ctas_per_sm, int32_t* dynamic, int32_t* aes_pair);
+
+/* Time every protect schedule on this batch (tile order x ctas_per_sm 1 .. 4 x dynamic x
+ * aes_pair, `reps` launches each after one warm-up, on `stream`) and keep the fastest.  The
+ * buffers are written to; their previous contents are lost.  Synchronises the device. */
 int fds_plan_autotune(fds_plan* plan, const uint8_t* pixels, int16_t* public_out,
                       uint8_t* private_out, int32_t reps, void* stream);
+
+/* The same for both directions, tuned separately: protect writes public_buf / private_buf,
+ * restore reads them and writes pixels_out (all three overwritten).  Each direction keeps
+ * its fastest ctas_per_sm / dynamic / aes_pair; the tile order, which the directions share,
+ * is the one with the smaller sum of their best times. */
+int fds_plan_autotune_directions(fds_plan* plan, const uint8_t* pixels, int16_t* public_buf,
+                                 uint8_t* private_buf, uint8_t* pixels_out, int32_t reps,
+                                 void* stream);
+
+/* The plan's schedule as a NUL-terminated JSON object: "size_class" (the key under which a
+ * caller may store it: "t<a>-T<b>-k<k>", 2^a the median image's tiles of 64 blocks and 2^b
+ * the batch's tiles, each rounded up to a power of two, k the uniform k or "mixed"),
+ * "largest_first", "protect" and "restore" ({"ctas_per_sm", "dynamic", "aes_pair"}), and
+ * "candidates": every schedule the last autotune timed with its mean ms per launch.
+ * *length (may be NULL) receives the size including the NUL; buf may be NULL to ask for it.
+ * FDS_E_INVALID when capacity is smaller than that size. */
+int fds_plan_schedule_json(const fds_plan* plan, char* buf, int64_t capacity, int64_t* length);
 
 /* One persistent launch protecting / restoring every image of the plan.  Buffer pointers
  * and offsets as for fds_protect / fds_restore. */

@@ -69,6 +69,13 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_int32)]),
     "fds_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "fds_plan_set_direction_schedule": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int32] * 4),
+    "fds_plan_get_direction_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]
+                                        + [ctypes.POINTER(ctypes.c_int32)] * 3),
+    "fds_plan_autotune_directions": (ctypes.c_int, [ctypes.c_void_p] * 5
+                                     + [ctypes.c_int32, ctypes.c_void_p]),
+    "fds_plan_schedule_json": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_int64)]),
     "fds_plan_protect": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "fds_plan_restore": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "fds_plan_protect_graph": (ctypes.c_int, [ctypes.c_void_p] * 5),

@@ -6,7 +6,9 @@ restore runs in the library's CUDA kernels.  Function names follow include/fds.h
 from __future__ import annotations
 
 import ctypes
+import json
 import math
+import os
 from dataclasses import dataclass
 from typing import Sequence
 
@@ -495,6 +497,9 @@ def sync() -> None:
     _lib.check(_lib.load().fds_sync(_stream_ptr(torch.device("cuda"))), "fds_sync")
 
 
+_DIRECTIONS = {"protect": 0, "restore": 1}
+
+
 class Plan:
     """fds_plan_*: a batch whose descriptors and tile schedule live on the device, run as one
     persistent launch (optionally through a CUDA graph)."""
@@ -530,22 +535,79 @@ class Plan:
         except Exception:
             pass
 
-    def set_schedule(self, ctas_per_sm: int = 2, dynamic: bool = False,
+    def set_schedule(self, ctas_per_sm: int = 0, dynamic: bool = False,
                      largest_first: bool = False) -> None:
+        """fds_plan_set_schedule: both directions (ctas_per_sm 0 = each kernel's residency)."""
         _lib.check(_lib.load().fds_plan_set_schedule(self._h, ctas_per_sm, int(dynamic),
                                                      int(largest_first)), "fds_plan_set_schedule")
 
     def schedule(self) -> tuple[int, int, int]:
+        """(ctas_per_sm, dynamic, largest_first) of the protect direction."""
         v = [ctypes.c_int32() for _ in range(3)]
         _lib.check(_lib.load().fds_plan_get_schedule(self._h, *(ctypes.byref(x) for x in v)),
                    "fds_plan_get_schedule")
         return tuple(x.value for x in v)
 
+    def set_direction_schedule(self, direction: str, ctas_per_sm: int = 0, dynamic: bool = False,
+                               aes_pair: bool = False) -> None:
+        """fds_plan_set_direction_schedule; direction "protect" or "restore"."""
+        _lib.check(_lib.load().fds_plan_set_direction_schedule(
+            self._h, _DIRECTIONS[direction], ctas_per_sm, int(dynamic), int(aes_pair)),
+            "fds_plan_set_direction_schedule")
+
+    def direction_schedule(self, direction: str) -> dict:
+        v = [ctypes.c_int32() for _ in range(3)]
+        _lib.check(_lib.load().fds_plan_get_direction_schedule(
+            self._h, _DIRECTIONS[direction], *(ctypes.byref(x) for x in v)),
+            "fds_plan_get_direction_schedule")
+        return {"ctas_per_sm": v[0].value, "dynamic": v[1].value, "aes_pair": v[2].value}
+
     def autotune(self, pixels, public_out, private_out, reps: int = 3) -> tuple[int, int, int]:
+        """fds_plan_autotune: protect only; returns schedule()."""
         _lib.check(_lib.load().fds_plan_autotune(self._h, pixels.data_ptr(), public_out.data_ptr(),
                                                  private_out.data_ptr(), reps,
                                                  _stream_ptr(pixels.device)), "fds_plan_autotune")
         return self.schedule()
+
+    def schedule_json(self) -> dict:
+        """fds_plan_schedule_json, parsed: size class, both directions, last candidates."""
+        n = ctypes.c_int64()
+        lib = _lib.load()
+        _lib.check(lib.fds_plan_schedule_json(self._h, None, 0, ctypes.byref(n)), "fds_plan_schedule_json")
+        buf = ctypes.create_string_buffer(n.value)
+        _lib.check(lib.fds_plan_schedule_json(self._h, buf, n.value, ctypes.byref(n)),
+                   "fds_plan_schedule_json")
+        return json.loads(buf.value.decode())
+
+    def tune(self, pixels, public_buf, private_buf, pixels_out, reps: int = 3,
+             cache: str | os.PathLike | None = None) -> dict:
+        """Per-direction schedule for this batch.  With `cache` (a JSON file of size class ->
+        schedule), a stored schedule of the batch's size class is applied without timing;
+        otherwise fds_plan_autotune_directions times every candidate (overwriting the three
+        buffers) and the choice is stored there.  Returns schedule_json() plus "cached"."""
+        store = {}
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                store = json.load(f)
+        cls = self.schedule_json()["size_class"]
+        if cls in store:
+            c = store[cls]
+            self.set_schedule(0, False, bool(c["largest_first"]))
+            for d in _DIRECTIONS:
+                self.set_direction_schedule(d, c[d]["ctas_per_sm"], bool(c[d]["dynamic"]),
+                                            bool(c[d]["aes_pair"]))
+            return dict(self.schedule_json(), cached=True)
+        _lib.check(_lib.load().fds_plan_autotune_directions(
+            self._h, pixels.data_ptr(), public_buf.data_ptr(), private_buf.data_ptr(),
+            pixels_out.data_ptr(), reps, _stream_ptr(pixels.device)), "fds_plan_autotune_directions")
+        out = self.schedule_json()
+        if cache is not None:
+            store[cls] = {k: out[k] for k in ("largest_first", "protect", "restore")}
+            tmp = f"{os.fspath(cache)}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(store, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(out, cached=False)
 
     def protect(self, pixels, public_out, private_out, graph: bool = False) -> None:
         fn = _lib.load().fds_plan_protect_graph if graph else _lib.load().fds_plan_protect

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -397,13 +398,13 @@ void set_tables(TileArgs& a, int dev) {
   a.counters = g_tables[dev].counters;
 }
 
-int run_protect(TileArgs& a, int dev, cudaStream_t s, bool debug, int per_sm = 2) {
+int run_protect(TileArgs& a, int dev, cudaStream_t s, bool debug, int per_sm = 0) {
   set_tables(a, dev);
   const cudaError_t e = launch_protect(a, s, debug, g_tables[dev].sms, per_sm);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "protect launch");
 }
 
-int run_restore(TileArgs& a, int dev, cudaStream_t s, int per_sm = 2) {
+int run_restore(TileArgs& a, int dev, cudaStream_t s, int per_sm = 0) {
   set_tables(a, dev);
   const cudaError_t e = launch_restore(a, s, g_tables[dev].sms, per_sm);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "restore launch");
@@ -1259,7 +1260,9 @@ struct fds_plan {
   int dev = 0;
   std::vector<fds_image> images;        // host copy, caller's order
   int32_t n = 0, total_tiles = 0, k_uniform = -1, capacity = 0;
-  int32_t per_sm = 2, dynamic = 0, largest_first = 0;
+  // schedule per direction (0 protect, 1 restore); per_sm 0 = the kernel's residency
+  int32_t per_sm[2] = {0, 0}, dynamic[2] = {0, 0}, aes_pair[2] = {0, 0}, largest_first = 0;
+  std::string tuning;                   // JSON list of the last autotune's candidates
   void* mem = nullptr;                  // device: BatchImage[cap], tile_start[cap+1], counter
   void* host = nullptr;                 // pinned staging of reusable plans (fds_plan_reserve)
   cudaEvent_t staged = nullptr;         // the last asynchronous update has left `host`
@@ -1351,21 +1354,22 @@ int plan_device(const fds_plan* p) {
   return FDS_OK;
 }
 
-TileArgs plan_args(const fds_plan* p) {
+TileArgs plan_args(const fds_plan* p, int dir) {
   TileArgs a{};
   a.images = p->d_images;
   a.tile_start = p->d_tile_start;
   a.n_images = p->n;
   a.total_tiles = p->total_tiles;
   a.k = p->k_uniform;
-  a.dispenser = p->dynamic ? p->d_dispenser : nullptr;
+  a.dispenser = p->dynamic[dir] ? p->d_dispenser : nullptr;
+  a.aes_pair = p->aes_pair[dir];
   return a;
 }
 
 // enqueue one protect (dir 0) or restore (dir 1) of the whole plan on s
 int plan_enqueue(fds_plan* p, int dir, const void* b0, const void* b1, const void* b2, cudaStream_t s) {
-  TileArgs a = plan_args(p);
-  if (p->dynamic) {
+  TileArgs a = plan_args(p, dir);
+  if (p->dynamic[dir]) {
     const cudaError_t e = cudaMemsetAsync(p->d_dispenser, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return cuda_fail(e, "counter reset");
   }
@@ -1373,12 +1377,43 @@ int plan_enqueue(fds_plan* p, int dir, const void* b0, const void* b1, const voi
     a.pixels_in = static_cast<const uint8_t*>(b0);
     a.pub_out = static_cast<int16_t*>(const_cast<void*>(b1));
     a.priv_out = static_cast<uint8_t*>(const_cast<void*>(b2));
-    return run_protect(a, p->dev, s, false, p->per_sm);
+    return run_protect(a, p->dev, s, false, p->per_sm[0]);
   }
   a.pub_in = static_cast<const int16_t*>(b0);
   a.priv_in = static_cast<const uint8_t*>(b1);
   a.pixels_out = static_cast<uint8_t*>(const_cast<void*>(b2));
-  return run_restore(a, p->dev, s, p->per_sm);
+  return run_restore(a, p->dev, s, p->per_sm[1]);
+}
+
+// size class of a batch, the key of stored schedules: the median image's tiles and the
+// batch's tiles, each rounded up to a power of two, and k when it is uniform
+std::string size_class(const fds_plan* p) {
+  std::vector<int64_t> t(p->n);
+  for (int i = 0; i < p->n; ++i)
+    t[i] = ((int64_t)(p->images[i].width / 8) * (p->images[i].height / 8) + kTileBlocks - 1) / kTileBlocks;
+  int64_t med = 0;
+  if (p->n) {
+    std::nth_element(t.begin(), t.begin() + p->n / 2, t.end());
+    med = t[p->n / 2];
+  }
+  auto lg = [](int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+  };
+  std::string c = "t" + std::to_string(lg(med)) + "-T" + std::to_string(lg(p->total_tiles)) + "-k";
+  return c + (p->k_uniform >= 0 ? std::to_string(p->k_uniform) : std::string("mixed"));
+}
+
+std::string dir_json(const fds_plan* p, int dir) {
+  return "{\"ctas_per_sm\": " + std::to_string(p->per_sm[dir]) + ", \"dynamic\": " + std::to_string(p->dynamic[dir]) +
+         ", \"aes_pair\": " + std::to_string(p->aes_pair[dir]) + "}";
+}
+
+std::string schedule_json(const fds_plan* p) {
+  return "{\"size_class\": \"" + size_class(p) + "\", \"largest_first\": " + std::to_string(p->largest_first) +
+         ", \"protect\": " + dir_json(p, 0) + ", \"restore\": " + dir_json(p, 1) + ", \"candidates\": [" +
+         p->tuning + "]}";
 }
 
 int plan_buffers_ok(const void* px, const void* pub, const void* priv) {
@@ -1413,6 +1448,93 @@ int plan_graph(fds_plan* p, int dir, const void* b0, const void* b1, const void*
   }
   const cudaError_t e = cudaGraphLaunch(p->graph[dir], s);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "graph launch");
+}
+
+// mean time of one launch of direction dir in the plan's current schedule (one warm-up)
+int time_direction(fds_plan* p, int dir, const void* b0, const void* b1, const void* b2, int reps, cudaStream_t s,
+                   cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  int rc = plan_enqueue(p, dir, b0, b1, b2, s);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = plan_enqueue(p, dir, b0, b1, b2, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  if (rc) return rc;
+  cudaEventElapsedTime(ms, e0, e1);
+  *ms /= (float)reps;
+  return FDS_OK;
+}
+
+// Time every schedule of protect (and of restore when px_out is given) on this batch and keep
+// the fastest.  Tile order is shared by the directions: the order with the smaller sum of the
+// two directions' best times wins.  Every candidate and its time is kept for the JSON export.
+int plan_autotune(fds_plan* p, const uint8_t* px, int16_t* pub, uint8_t* priv, uint8_t* px_out, int reps,
+                  cudaStream_t s) {
+  if (!p) return set_err(FDS_E_INVALID, "null plan");
+  if (reps < 1) return set_err(FDS_E_INVALID, "reps must be >= 1");
+  int rc = plan_device(p);
+  if (!rc) rc = plan_buffers_ok(px, pub, priv);
+  if (!rc && px_out) rc = plan_buffers_ok(px_out, pub, priv);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return set_err(FDS_E_CUDA, "event creation failed");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_err(FDS_E_CUDA, "event creation failed");
+  }
+  const int ndir = px_out ? 2 : 1;
+  struct Best {
+    float ms = 1e30f;
+    int ps = 0, dyn = 0, aes = 0;
+  } best[2][2];
+  std::string list;
+  for (int lf = 0; lf < 2 && !rc; ++lf) {
+    if (lf != p->largest_first) {
+      p->largest_first = lf;
+      const cudaError_t e = cudaDeviceSynchronize();   // in-flight launches read the tables
+      rc = e != cudaSuccess ? cuda_fail(e, "synchronize") : upload_schedule(p);
+    }
+    for (int dir = 0; dir < ndir && !rc; ++dir) {
+      const int cap = dir == 0 ? FDS_PROTECT_MAX_CTAS_PER_SM : FDS_RESTORE_MAX_CTAS_PER_SM;
+      for (int ps = 1; ps <= cap && !rc; ++ps)
+        for (int dyn = 0; dyn < 2 && !rc; ++dyn)
+          for (int aes = 0; aes < 2 && !rc; ++aes) {
+            p->per_sm[dir] = ps, p->dynamic[dir] = dyn, p->aes_pair[dir] = aes;
+            float ms = 0.0f;
+            rc = dir == 0 ? time_direction(p, 0, px, pub, priv, reps, s, e0, e1, &ms)
+                          : time_direction(p, 1, pub, priv, px_out, reps, s, e0, e1, &ms);
+            if (rc) break;
+            if (ms < best[lf][dir].ms) best[lf][dir] = {ms, ps, dyn, aes};
+            char row[192];
+            std::snprintf(row, sizeof(row),
+                          "%s{\"direction\": \"%s\", \"largest_first\": %d, \"ctas_per_sm\": %d, \"dynamic\": %d, "
+                          "\"aes_pair\": %d, \"ms\": %.5f}",
+                          list.empty() ? "" : ", ", dir ? "restore" : "protect", lf, ps, dyn, aes, ms);
+            list += row;
+          }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  float t0 = 0.0f, t1 = 0.0f;
+  for (int dir = 0; dir < ndir; ++dir) t0 += best[0][dir].ms, t1 += best[1][dir].ms;
+  const int lf = t1 < t0 ? 1 : 0;
+  for (int dir = 0; dir < ndir; ++dir) {
+    p->per_sm[dir] = best[lf][dir].ps;
+    p->dynamic[dir] = best[lf][dir].dyn;
+    p->aes_pair[dir] = best[lf][dir].aes;
+  }
+  p->tuning = list;
+  if (lf != p->largest_first) {
+    p->largest_first = lf;
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return upload_schedule(p);
+  }
+  drop_graphs(p);
+  return FDS_OK;
 }
 
 }  // namespace
@@ -1523,11 +1645,15 @@ int fds_plan_update(fds_plan* plan, const fds_image* images, int32_t n, void* st
 
 int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic, int32_t largest_first) {
   if (!plan) return set_err(FDS_E_INVALID, "null plan");
-  if (ctas_per_sm != 1 && ctas_per_sm != 2) return set_err(FDS_E_INVALID, "ctas_per_sm must be 1 or 2");
+  if (ctas_per_sm < 0 || ctas_per_sm > FDS_PROTECT_MAX_CTAS_PER_SM)
+    return set_err(FDS_E_INVALID, "ctas_per_sm must be 0 .. 4");
   int rc = plan_device(plan);
   if (rc) return rc;
-  plan->per_sm = ctas_per_sm;
-  plan->dynamic = dynamic ? 1 : 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    plan->per_sm[dir] = dir == 1 && ctas_per_sm > FDS_RESTORE_MAX_CTAS_PER_SM ? 0 : ctas_per_sm;
+    plan->dynamic[dir] = dynamic ? 1 : 0;
+    plan->aes_pair[dir] = 0;
+  }
   const int lf = largest_first ? 1 : 0;
   if (lf != plan->largest_first) {
     plan->largest_first = lf;
@@ -1541,9 +1667,35 @@ int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic, 
 
 int fds_plan_get_schedule(const fds_plan* plan, int32_t* ctas_per_sm, int32_t* dynamic, int32_t* largest_first) {
   if (!plan) return set_err(FDS_E_INVALID, "null plan");
-  if (ctas_per_sm) *ctas_per_sm = plan->per_sm;
-  if (dynamic) *dynamic = plan->dynamic;
+  if (ctas_per_sm) *ctas_per_sm = plan->per_sm[0];
+  if (dynamic) *dynamic = plan->dynamic[0];
   if (largest_first) *largest_first = plan->largest_first;
+  return FDS_OK;
+}
+
+int fds_plan_set_direction_schedule(fds_plan* plan, int32_t direction, int32_t ctas_per_sm, int32_t dynamic,
+                                    int32_t aes_pair) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  if (direction != 0 && direction != 1) return set_err(FDS_E_INVALID, "direction must be 0 (protect) or 1 (restore)");
+  const int cap = direction == 0 ? FDS_PROTECT_MAX_CTAS_PER_SM : FDS_RESTORE_MAX_CTAS_PER_SM;
+  if (ctas_per_sm < 0 || ctas_per_sm > cap)
+    return set_err(FDS_E_INVALID, "ctas_per_sm must be 0 .. " + std::to_string(cap) + " for this direction");
+  int rc = plan_device(plan);
+  if (rc) return rc;
+  plan->per_sm[direction] = ctas_per_sm;
+  plan->dynamic[direction] = dynamic ? 1 : 0;
+  plan->aes_pair[direction] = aes_pair ? 1 : 0;
+  drop_graphs(plan);
+  return FDS_OK;
+}
+
+int fds_plan_get_direction_schedule(const fds_plan* plan, int32_t direction, int32_t* ctas_per_sm,
+                                    int32_t* dynamic, int32_t* aes_pair) {
+  if (!plan) return set_err(FDS_E_INVALID, "null plan");
+  if (direction != 0 && direction != 1) return set_err(FDS_E_INVALID, "direction must be 0 (protect) or 1 (restore)");
+  if (ctas_per_sm) *ctas_per_sm = plan->per_sm[direction];
+  if (dynamic) *dynamic = plan->dynamic[direction];
+  if (aes_pair) *aes_pair = plan->aes_pair[direction];
   return FDS_OK;
 }
 
@@ -1581,41 +1733,23 @@ int fds_plan_restore_graph(fds_plan* plan, const int16_t* public_in, const uint8
 
 int fds_plan_autotune(fds_plan* plan, const uint8_t* pixels, int16_t* public_out, uint8_t* private_out,
                       int32_t reps, void* stream) {
+  return fds::plan_autotune(plan, pixels, public_out, private_out, nullptr, reps, (cudaStream_t)stream);
+}
+
+int fds_plan_autotune_directions(fds_plan* plan, const uint8_t* pixels, int16_t* public_buf,
+                                 uint8_t* private_buf, uint8_t* pixels_out, int32_t reps, void* stream) {
+  if (!pixels_out) return set_err(FDS_E_INVALID, "null buffer");
+  return fds::plan_autotune(plan, pixels, public_buf, private_buf, pixels_out, reps, (cudaStream_t)stream);
+}
+
+int fds_plan_schedule_json(const fds_plan* plan, char* buf, int64_t capacity, int64_t* length) {
   if (!plan) return set_err(FDS_E_INVALID, "null plan");
-  if (reps < 1) return set_err(FDS_E_INVALID, "reps must be >= 1");
-  int rc = plan_device(plan);
-  if (!rc) rc = plan_buffers_ok(pixels, public_out, private_out);
-  if (rc) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return set_err(FDS_E_CUDA, "event creation failed");
-  float best = 1e30f;
-  int32_t bps = 2, bdyn = 0, blf = 0;
-  for (int lf = 0; lf < 2 && !rc; ++lf)
-    for (int dyn = 0; dyn < 2 && !rc; ++dyn)
-      for (int ps = 1; ps <= 2 && !rc; ++ps) {
-        if ((rc = fds_plan_set_schedule(plan, ps, dyn, lf))) break;
-        if ((rc = plan_enqueue(plan, 0, pixels, public_out, private_out, s))) break;   // warm-up
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && !rc; ++r) rc = plan_enqueue(plan, 0, pixels, public_out, private_out, s);
-        cudaEventRecord(e1, s);
-        const cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-          rc = cuda_fail(e, "autotune timing");
-          break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          bps = ps, bdyn = dyn, blf = lf;
-        }
-      }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (rc) return rc;
-  return fds_plan_set_schedule(plan, bps, bdyn, blf);
+  const std::string j = fds::schedule_json(plan);
+  if (length) *length = (int64_t)j.size() + 1;
+  if (!buf) return FDS_OK;
+  if (capacity < (int64_t)j.size() + 1) return set_err(FDS_E_INVALID, "buffer too small for the schedule");
+  std::memcpy(buf, j.c_str(), j.size() + 1);
+  return FDS_OK;
 }
 
 }  // extern "C"
@@ -1734,5 +1868,5 @@ extern "C" int fds_protect_batch_noalloc(const uint8_t* pixels, int16_t* public_
   a.total_tiles = (int32_t)acc;
   a.k = k_uniform;
   a.dispenser = d_counter;
-  return run_protect(a, dev, s, false, 2);
+  return run_protect(a, dev, s, false);
 }

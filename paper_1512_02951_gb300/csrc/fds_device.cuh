@@ -365,6 +365,45 @@ __device__ __forceinline__ void aes128_encrypt_rep_n(uint32_t (&s)[M][4], const 
   }
 }
 
+// aes128_encrypt on M independent blocks, their rounds interleaved (the same four shared
+// T-tables): a thread with M blocks overlaps their table-lookup latencies.
+template <int M>
+__device__ __forceinline__ void aes128_encrypt_n(uint32_t (&s)[M][4], const uint32_t* rk, const uint32_t* T) {
+  const char* Tc = reinterpret_cast<const char*>(T);
+  auto t0 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + ((w << 2) & 0x3fcu)); };
+  auto t1 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + 1024 + ((w >> 6) & 0x3fcu)); };
+  auto t2 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + 2048 + ((w >> 14) & 0x3fcu)); };
+  auto t3 = [&](uint32_t w) { return *reinterpret_cast<const uint32_t*>(Tc + 3072 + ((w >> 22) & 0x3fcu)); };
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[m][c] ^= rk[c];
+#pragma unroll 1
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t k0 = rk[4 * r], k1 = rk[4 * r + 1], k2 = rk[4 * r + 2], k3 = rk[4 * r + 3];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const uint32_t s0 = s[m][0], s1 = s[m][1], s2 = s[m][2], s3 = s[m][3];
+      s[m][0] = t0(s0) ^ t1(s1) ^ t2(s2) ^ t3(s3) ^ k0;
+      s[m][1] = t0(s1) ^ t1(s2) ^ t2(s3) ^ t3(s0) ^ k1;
+      s[m][2] = t0(s2) ^ t1(s3) ^ t2(s0) ^ t3(s1) ^ k2;
+      s[m][3] = t0(s3) ^ t1(s0) ^ t2(s1) ^ t3(s2) ^ k3;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const uint32_t s0 = s[m][0], s1 = s[m][1], s2 = s[m][2], s3 = s[m][3];
+    s[m][0] = (__byte_perm(t0(s0), 0u, 0x4441u) | __byte_perm(t0(s1 >> 8), 0u, 0x4414u) |
+               __byte_perm(t0(s2 >> 16), 0u, 0x4144u) | __byte_perm(t0(s3 >> 24), 0u, 0x1444u)) ^ rk[40];
+    s[m][1] = (__byte_perm(t0(s1), 0u, 0x4441u) | __byte_perm(t0(s2 >> 8), 0u, 0x4414u) |
+               __byte_perm(t0(s3 >> 16), 0u, 0x4144u) | __byte_perm(t0(s0 >> 24), 0u, 0x1444u)) ^ rk[41];
+    s[m][2] = (__byte_perm(t0(s2), 0u, 0x4441u) | __byte_perm(t0(s3 >> 8), 0u, 0x4414u) |
+               __byte_perm(t0(s0 >> 16), 0u, 0x4144u) | __byte_perm(t0(s1 >> 24), 0u, 0x1444u)) ^ rk[42];
+    s[m][3] = (__byte_perm(t0(s3), 0u, 0x4441u) | __byte_perm(t0(s0 >> 8), 0u, 0x4414u) |
+               __byte_perm(t0(s1 >> 16), 0u, 0x4144u) | __byte_perm(t0(s2 >> 24), 0u, 0x1444u)) ^ rk[43];
+  }
+}
+
 // Counter block IV + n (128-bit big-endian addition) as four state columns.
 // iv_hi / iv_lo: the IV's bytes 0..7 / 8..15 read as big-endian integers.
 __device__ __forceinline__ void ctr_block(uint64_t iv_hi, uint64_t iv_lo, uint64_t n,

@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
       if (!a.plain_private)
         ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
                  ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
-                 BATCH ? sl->rk : a.rk, Ts);
+                 BATCH ? sl->rk : a.rk, Ts, BATCH && a.aes_pair);
     }
     fence_proxy_async();
     have_prev = true;
@@ -544,7 +544,7 @@ static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_
   cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, kSmemBytes, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
-  const int cap = (per_sm == 1 ? 1 : kPCtasPerSm) * sms;
+  const int cap = (per_sm >= 1 && per_sm < kPCtasPerSm ? per_sm : kPCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
   if (grid > 0) protect_kernel<K, DEBUG, BATCH, PACK><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();

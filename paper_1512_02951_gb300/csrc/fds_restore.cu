@@ -236,10 +236,10 @@ __device__ __forceinline__ void wait_fragments(const TileSlot* sl, uint64_t* bar
 
 // CTR decryption of the private range of slot sl's tile, in staging area st
 __device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint32_t* rk, uint8_t* st,
-                                                  const uint32_t* Ts) {
+                                                  const uint32_t* Ts, bool aes_pair = false) {
   const int k = sl->k;
   ctr_tile(st + kTileCb * 2 * (63 - k), sl->nb * 6 * (k + 1),
-           ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl, rk, Ts);
+           ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl, rk, Ts, aes_pair);
 }
 
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
     load_fragments<PUBIMG>(slot(0), stage(0), bars);
     wait_fragments<PUBIMG>(slot(0), bars, phase[0], lost);
     __syncthreads();
-    if (!PUBIMG && !a.plain_private) decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts);
+    if (!PUBIMG && !a.plain_private)
+      decrypt_fragments(slot(0), BATCH ? slot(0)->rk : a.rk, stage(0), Ts, BATCH && a.aes_pair);
   }
   int esc = 0;
   bool fail = false;
@@ -434,7 +435,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
         unpack_tile<PACK>(slot((it + 1) % 3), land, stage(buf ^ 1));
       }
     } else if (!PUBIMG && nxt < ntiles && !a.plain_private) {
-      decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts);
+      decrypt_fragments(slot((it + 1) % 3), BATCH ? slot((it + 1) % 3)->rk : a.rk, stage(buf ^ 1), Ts,
+                        BATCH && a.aes_pair);
     }
     fence_proxy_async();                                  // pixel writes before the bulk stores
     const bool skip = __syncthreads_or(cur_lost != 0);                     // C
@@ -482,7 +484,7 @@ static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_
   cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG, PACK>, smem, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
-  const int cap = (per_sm == 1 ? 1 : kCtasPerSm) * sms;
+  const int cap = (per_sm >= 1 && per_sm < kCtasPerSm ? per_sm : kCtasPerSm) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
   if (grid > 0) restore_kernel<K, BATCH, PUBIMG, PACK><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();

@@ -101,6 +101,8 @@ struct TileArgs {
   int32_t pack;
   // restore in the public-image form (one image): private positions zero, DC 1024
   int32_t public_image;
+  // AES lane schedule of the batched form: nonzero = two keystream blocks per thread
+  int32_t aes_pair;
 };
 
 // What a CTA knows about the tile it is working on (shared memory, filled one tile ahead).
@@ -122,9 +124,10 @@ struct TileSlot {
 constexpr int32_t kPxIn16 = 1, kPxOut16 = 2;
 
 // launchers (one translation unit each); `sms` = number of SMs of the device, `per_sm` =
-// resident CTAs per SM to launch (1 or 2)
-cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 2);
-cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 2);
+// CTAs per SM to launch, at most the kernel's residency (protect 4, restore 2); 0 = that
+// residency
+cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 0);
+cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 0);
 // tensor-core protect of one image (form 0: BF16 three limbs, 1: TF32 two limbs); tiles of
 // 128 channel-blocks, two CTAs per SM
 cudaError_t launch_protect_tc(const TileArgs& a, cudaStream_t s, int form, bool debug, int sms);
@@ -300,10 +303,34 @@ __device__ __forceinline__ void load_row_shifted(const uint8_t* tile, int y, int
 
 // AES-128-CTR over `bytes` bytes of a 16-byte aligned staging area whose first byte is byte
 // 16 * first_block of the image's private message.
-// The IV comes from the tile's slot; rk are the 44 round keys.
+// The IV comes from the tile's slot; rk are the 44 round keys.  aes_pair: each thread takes
+// two keystream blocks, i and i + kThreads, encrypted interleaved (the lane schedule the
+// batched form's autotuner can choose), instead of one.
 __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_block,
-                                         const TileSlot* sl, const uint32_t* rk, const uint32_t* Ts) {
+                                         const TileSlot* sl, const uint32_t* rk, const uint32_t* Ts,
+                                         bool aes_pair = false) {
   const int nblk = (bytes + 15) >> 4;
+  if (aes_pair) {
+    for (int i = threadIdx.x; i < nblk; i += 2 * kThreads) {
+      const bool two = i + kThreads < nblk;
+      uint32_t s[2][4];
+      ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s[0]);
+      ctr_block(sl->iv_hi, sl->iv_lo, first_block + i + kThreads, s[1]);
+      aes128_encrypt_n<2>(s, rk, Ts);
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        if (m == 1 && !two) break;
+        uint4* p = reinterpret_cast<uint4*>(st + 16 * (i + m * kThreads));
+        uint4 d = *p;
+        d.x ^= s[m][0];
+        d.y ^= s[m][1];
+        d.z ^= s[m][2];
+        d.w ^= s[m][3];
+        *p = d;
+      }
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < nblk; i += kThreads) {
     uint32_t s[4];
     ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s);

@@ -114,6 +114,11 @@ def test_plan_arguments_are_checked_on_the_host(lib):
     d[0].key_slot, d[0].public_offset = 0, 8
     assert lib.fds_plan_create(d, 1, ctypes.byref(h)) in (-1, -2)           # misaligned offset
     assert lib.fds_plan_set_schedule(None, 1, 0, 0) == -1
+    assert lib.fds_plan_set_direction_schedule(None, 0, 1, 0, 0) == -1
+    assert lib.fds_plan_get_direction_schedule(None, 1, None, None, None) == -1
+    assert lib.fds_plan_autotune_directions(None, None, None, None, None, 1, None) == -1
+    n = ctypes.c_int64()
+    assert lib.fds_plan_schedule_json(None, None, 0, ctypes.byref(n)) == -1
     assert lib.fds_plan_destroy(None) == 0
 
 

@@ -112,13 +112,69 @@ def test_plan_graph_replay_and_autotune(api):
     pub = torch.empty(npub, dtype=torch.uint8, device=DEV)
     priv = torch.empty(npriv, dtype=torch.uint8, device=DEV)
     ps, dyn, lf = plan.autotune(px, pub, priv, reps=2)
-    assert ps in (1, 2) and dyn in (0, 1) and lf in (0, 1)
+    assert 1 <= ps <= 4 and dyn in (0, 1) and lf in (0, 1)
     _same(descs, want, _plan_run(plan, px, npub, npriv, graph=True, bufs=bufs))
     _same(descs, want, _plan_run(plan, px, npub, npriv, graph=False))
     plan.close()
     for d in descs:
         api.key_release(d.key_slot)
     assert rng is not None
+
+
+@pytest.mark.parametrize("ks", [[5] * len(SIZES), [0, 5, 17, 63, 5, 0, 9, 1, 5, 0]])
+def test_plan_direction_schedules_and_aes_lane_pairs(api, ks):
+    """Every per-direction schedule (protect 1..4 CTAs/SM, restore 1..2, static or dynamic,
+    one or two keystream blocks per thread) gives the per-image bytes; k = 17 and 63 tiles
+    have more keystream blocks than a CTA has threads, where the paired schedule differs."""
+    descs, imgs, keys, px, npub, npriv = _batch(api, SIZES, ks, seed=23)
+    want = _per_image(api, descs, px, npub, npriv)
+    plan = api.Plan(descs)
+    for ps, rs in ((1, 1), (2, 2), (3, 1), (4, 2), (0, 0)):
+        for dyn in (0, 1):
+            for aes in (0, 1):
+                plan.set_direction_schedule("protect", ps, bool(dyn), bool(aes))
+                plan.set_direction_schedule("restore", rs, bool(1 - dyn), bool(aes))
+                assert plan.direction_schedule("protect") == {"ctas_per_sm": ps, "dynamic": dyn, "aes_pair": aes}
+                _same(descs, want, _plan_run(plan, px, npub, npriv))
+    from paper_1512_02951_gb300 import _lib
+    with pytest.raises(_lib.FdsError):
+        plan.set_direction_schedule("restore", 3)
+    plan.close()
+    for d in descs:
+        api.key_release(d.key_slot)
+
+
+def test_plan_tunes_both_directions_and_caches_the_choice(api, tmp_path):
+    import json
+
+    sizes = [(int(w), int(h)) for w, h in synth.batch_sizes(60, 91, 64, 512)]
+    descs, imgs, keys, px, npub, npriv = _batch(api, sizes, [0] * len(sizes), seed=41)
+    want = _per_image(api, descs, px, npub, npriv)
+    plan = api.Plan(descs)
+    bufs = (torch.empty(npub, dtype=torch.uint8, device=DEV),
+            torch.empty(npriv, dtype=torch.uint8, device=DEV), torch.empty_like(px))
+    cache = tmp_path / "schedules.json"
+    got = plan.tune(px, *bufs, reps=2, cache=cache)
+    assert got["cached"] is False
+    cands = got["candidates"]
+    assert len(cands) == 2 * (4 * 2 * 2 + 2 * 2 * 2)        # tile orders x protect + restore grids
+    assert all(c["ms"] > 0 for c in cands)
+    for d in ("protect", "restore"):                         # the kept schedule is the fastest
+        best = min((c for c in cands if c["direction"] == d and c["largest_first"] == got["largest_first"]),
+                   key=lambda c: c["ms"])
+        assert got[d] == {k: best[k] for k in ("ctas_per_sm", "dynamic", "aes_pair")}
+    _same(descs, want, _plan_run(plan, px, npub, npriv))
+    stored = json.loads(cache.read_text())
+    assert list(stored) == [got["size_class"]]
+    plan2 = api.Plan(descs)
+    again = plan2.tune(px, *bufs, cache=cache)
+    assert again["cached"] is True and again["candidates"] == []
+    assert {k: again[k] for k in ("largest_first", "protect", "restore")} == stored[got["size_class"]]
+    _same(descs, want, _plan_run(plan2, px, npub, npriv, graph=True))
+    plan.close()
+    plan2.close()
+    for d in descs:
+        api.key_release(d.key_slot)
 
 
 def test_plan_rejects_bad_descriptors(api):
