@@ -18,12 +18,14 @@
 //
 // Near ties are not decided inside the tile loop (one exact decision there held every thread
 // of the CTA at a barrier): each is recorded (tile, channel-block, position, the
-// float32-rounded value that was stored; 192 per CTA) and, once the CTA's tiles have all left, decided
-// exactly (integer coordinates in Z[cos(pi/16)]) from the image in global memory; a changed
-// value is patched into the fragment by XOR with (old ^ new), which is right for the public
-// int16 and, CTR being a stream cipher, for the private ciphertext alike.  The packed forms
-// patch the field's code difference into the bit streams (one thread per CTA: fields share
-// bytes).  A full list means the value is decided in place, from the tile in shared memory.
+// float32-rounded value that was stored; 192 per CTA) and, when the list is half full at the
+// start of a tile (int16 storage) and once the CTA's tiles have all left, decided exactly
+// (integer coordinates in Z[cos(pi/16)]) from the image in global memory, after the recorded
+// tiles' fragments have landed; a changed value is patched into the fragment by XOR with
+// (old ^ new), which is right for the public int16 and, CTR being a stream cipher, for the
+// private ciphertext alike.  The packed forms patch the field's code difference into the bit
+// streams (one thread per CTA: fields share bytes) at the end only.  A full list means the
+// value is decided in place, from the tile in shared memory.
 //
 // Packed storage (Sect. 6.4.3, Table 5; PACK = 11 or 8 bits per AC field): after step 1 the
 // staging area is packed in place into the tile's part of the two bit streams (DC unsigned in
@@ -340,6 +342,29 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
       bulk_wait_read_all();                  // the staging area may be written again
     }
     __syncthreads();                                                       // A'
+    if constexpr (PACK == 0 && !DEBUG) {
+      // the near-tie list half full: every earlier tile's fragments have been stored (the last
+      // private part just above), so the recorded values are decided and patched now
+      const int nrec = misc[0];
+      if (nrec >= kDeferCap / 2) {
+        if (t == 0) {
+          bulk_wait_all();
+          asm volatile("fence.proxy.async.global;\n" ::: "memory");   // bulk writes, then the patches
+        }
+        __syncthreads();                 // every thread has read misc[0] before arriving here
+        if (t == 0) {
+          misc[1] += nrec;
+          misc[0] = 0;
+        }
+        int esc = 0;
+        bool fail = false;
+        for (int i = t; i < min(nrec, kDeferCap); i += kThreads)
+          resolve_deferred<BATCH, 0>(a, deferred[i], &esc, &fail, nullptr);
+        if (esc) atomicAdd(&misc[2], esc);
+        if (fail) atomicAdd(&misc[3], 1);
+        __syncthreads();
+      }
+    }
 
     if (nxt < ntiles) load_pixels(slot(s_nxt), smem + kSmemPix + (buf ^ 1) * kPixBytes);
 
@@ -541,10 +566,12 @@ __global__ void __launch_bounds__(kThreads, kPCtasPerSm) protect_kernel(const __
 template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
+  static int resident[kMaxAttrDevices];
   cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, kSmemBytes, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
-  const int cap = (per_sm >= 1 && per_sm < kPCtasPerSm ? per_sm : kPCtasPerSm) * sms;
+  const int r = resident_ctas(protect_kernel<K, DEBUG, BATCH, PACK>, kThreads, kSmemBytes, resident);
+  const int cap = (per_sm >= 1 && per_sm < r ? per_sm : r) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
   if (grid > 0) protect_kernel<K, DEBUG, BATCH, PACK><<<grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();

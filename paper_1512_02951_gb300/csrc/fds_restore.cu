@@ -30,6 +30,7 @@
 
 namespace fds {
 
+constexpr int kRCtasPerSm = 2;
 constexpr int kSmemCoef = 0;                                 // 2 fragment staging areas
 constexpr int kSmemPix = kSmemCoef + 2 * kCoefBytes;         // 2 pixel tiles
 constexpr int kSmemQueue = kSmemPix + 2 * kPixBytes;
@@ -245,7 +246,7 @@ __device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
 // from the kernel parameters, which AES then takes as constant-bank operands)
 template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
+__global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) uint32_t Ts[1024];                // AES T-tables
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + kSmemQueue);
@@ -480,11 +481,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) restore_kernel(const __g
 template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
+  static int resident[kMaxAttrDevices];
   constexpr int smem = PACK ? kSmemBytesPacked : kSmemBytes;
   cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG, PACK>, smem, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
-  const int cap = (per_sm >= 1 && per_sm < kCtasPerSm ? per_sm : kCtasPerSm) * sms;
+  const int r = resident_ctas(restore_kernel<K, BATCH, PUBIMG, PACK>, kThreads, smem, resident);
+  const int cap = (per_sm >= 1 && per_sm < r ? per_sm : r) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
   if (grid > 0) restore_kernel<K, BATCH, PUBIMG, PACK><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();

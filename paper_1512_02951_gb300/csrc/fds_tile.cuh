@@ -26,7 +26,6 @@ constexpr int kRowBytes = kTileBlocks * 24;    // one pixel row of the tile (8 p
 constexpr int kPixBytes = 8 * kRowBytes;       // 12 KB
 constexpr int kCoefBytes = kTileCb * 128;      // public + private int16 staging (64 per cb)
 constexpr int kQueueCap = 256;                 // near-tie entries per tile
-constexpr int kCtasPerSm = 2;
 
 // tensor-core form: bytes of the B operand (basis limbs) in shared memory
 constexpr int kTcBBytesBf16 = 192 * 128;      // 3 limbs x 64 rows x 64 bf16
@@ -147,6 +146,20 @@ inline cudaError_t smem_attr_once(Kernel kernel, int bytes, bool (&done)[kMaxAtt
     done[dev] = true;
   }
   return cudaSuccess;
+}
+
+// Resident CTAs per SM of `kernel` at `threads` threads and `bytes` dynamic shared memory on
+// the current device (at least 1), cached per device in `cache` (0 = not yet asked)
+template <typename Kernel>
+inline int resident_ctas(Kernel kernel, int threads, int bytes, int (&cache)[kMaxAttrDevices]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxAttrDevices) return 1;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, bytes) != cudaSuccess || n < 1) n = 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
 }
 
 inline int total_tiles(const TileArgs& a) {

@@ -287,9 +287,9 @@ def test_beyond_4gib_sampled(api, k):
     torch.cuda.empty_cache()
 
 
-def test_queue_overflow_forward(api):
-    # a block with exact ties at several irrational positions, repeated over whole tiles, puts
-    # more near-ties into one tile than its queue holds
+def _tie_block():
+    """A pixel block whose DCT has exact ties (x.5) at several irrational positions (found
+    with the oracle's exact coordinates), and how many."""
     from oracle import exact
     rng = np.random.default_rng(77)
     cand = rng.integers(0, 3, (400000, 8, 8))
@@ -303,6 +303,13 @@ def test_queue_overflow_forward(api):
         if cnt > best_n:
             best, best_n = cand[i], cnt
     assert best_n >= 2
+    return best, best_n
+
+
+def test_queue_overflow_forward(api):
+    # a block with exact ties at several irrational positions, repeated over whole tiles, puts
+    # more near-ties into one tile than its queue holds
+    best, best_n = _tie_block()
     blocks = np.broadcast_to(best.astype(np.uint8), (8, 64, 3, 8, 8))
     img = odct.blocks_to_image(np.ascontiguousarray(blocks))
     api.counters(reset=True)
@@ -323,3 +330,43 @@ def test_queue_overflow_inverse(api):
     got = _gpu_restore(api, pub, priv, w, h, k, key, iv)
     want = ofds.restore(pub, priv, key, iv, k, w, h)
     assert np.array_equal(got, want)
+
+
+def test_near_tie_records_flush_and_overflow_forward(api):
+    """4096 x 1024 of the tie block: 1024 tiles, so CTAs run two tiles and more, every tile fills
+    the near-tie list (decided in place beyond it) and the list is flushed between tiles.  Every
+    block's public fragment must equal the oracle's for the block alone, every decrypted DC too."""
+    best, best_n = _tie_block()
+    w, h, k = 4096, 1024, 0
+    one = np.ascontiguousarray(np.broadcast_to(best.astype(np.uint8)[:, :, None], (8, 8, 3)))
+    key, iv = synth.make_key(81), synth.make_iv(82)
+    want_pub, want_priv = ofds.protect(one, key, iv, k)
+    want_dc = np.frombuffer(oaes.ctr_xcrypt(key, iv, want_priv), dtype="<i2")     # 3 DC values
+    img = np.ascontiguousarray(np.broadcast_to(one.reshape(1, 8, 1, 8, 3), (h // 8, 8, w // 8, 8, 3)).reshape(h, w, 3))
+    api.counters(reset=True)
+    pub, priv = _gpu_protect(api, img, key, iv, k)
+    ties = api.counters()[0]
+    assert np.array_equal(pub, np.broadcast_to(want_pub.reshape(1, 1, 3, 63 - k), pub.shape))
+    dc = np.frombuffer(oaes.ctr_xcrypt(key, iv, priv), dtype="<i2").reshape(h // 8, w // 8, 3)
+    assert np.array_equal(dc, np.broadcast_to(want_dc, dc.shape))
+    assert ties >= (h // 8) * (w // 8) * 3 * 2        # 384 a tile or more: the list of 192 overflows
+
+
+def test_near_tie_queue_overflow_inverse_whole_tiles(api):
+    """4096 x 1024 of DC-only blocks with DC = 4 (mod 8): every pixel is an exact .5, so every
+    tile (1024, several a CTA) overflows its near-tie queue and decides the rest in place.  A DC-only block (stored DC = F[0][0] + 1024) restores to round(DC / 8)
+    exactly (half away from zero), clamped to [0, 255]."""
+    w, h, k = 4096, 1024, 0
+    rng = np.random.default_rng(6)
+    dc = (8 * rng.integers(-40, 300, (h // 8, w // 8, 3)) + 4).astype(np.int64)    # both clamps
+    pub = np.zeros((h // 8, w // 8, 3, 63 - k), dtype=np.int16)
+    key, iv = synth.make_key(17), synth.make_iv(18)
+    priv = oaes.ctr_xcrypt(key, iv, dc.astype("<i2").tobytes())
+    api.counters(reset=True)
+    got = _gpu_restore(api, pub, priv, w, h, k, key, iv)
+    v2 = dc // 4                                       # 2 DC / 8, an odd integer
+    m = np.where(v2 > 0, (v2 + 1) // 2, -((-v2 + 1) // 2))   # half away from zero
+    want = np.clip(m, 0, 255).astype(np.uint8)
+    want = np.repeat(np.repeat(want, 8, axis=0), 8, axis=1)
+    assert np.array_equal(got, want)
+    assert api.counters()[0] >= 0.6 * w * h * 3        # all but the clamped blocks (a quarter)
