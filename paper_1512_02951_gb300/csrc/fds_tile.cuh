@@ -358,6 +358,35 @@ __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_
   }
 }
 
+// ctr_tile with the lane-replicated T0 table (kTrepWords words at Trep, entry x of copy L at
+// word 32 x + L): every lookup of a warp hits 32 distinct banks.  aes_pair as in ctr_tile.
+__device__ __forceinline__ void ctr_tile_rep(uint8_t* st, int bytes, uint64_t first_block, const TileSlot* sl,
+                                             const uint32_t* rk, const uint32_t* Trep, bool aes_pair = false) {
+  const int nblk = (bytes + 15) >> 4;
+  const char* Tl = reinterpret_cast<const char*>(Trep) + 4 * (threadIdx.x & 31);
+  const int step = aes_pair ? 2 * kThreads : kThreads;
+  for (int i = threadIdx.x; i < nblk; i += step) {
+    const int m_n = aes_pair && i + kThreads < nblk ? 2 : 1;
+    uint32_t s[2][4];
+    ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s[0]);
+    if (aes_pair) {
+      ctr_block(sl->iv_hi, sl->iv_lo, first_block + i + kThreads, s[1]);
+      aes128_encrypt_rep_n<2>(s, rk, Tl);
+    } else {
+      aes128_encrypt_rep(s[0], rk, Tl);
+    }
+    for (int m = 0; m < m_n; ++m) {
+      uint4* p = reinterpret_cast<uint4*>(st + 16 * (i + m * kThreads));
+      uint4 d = *p;
+      d.x ^= s[m][0];
+      d.y ^= s[m][1];
+      d.z ^= s[m][2];
+      d.w ^= s[m][3];
+      *p = d;
+    }
+  }
+}
+
 // ---- packed storage (Sect. 6.4.3): a full tile's 192 channel-blocks are a multiple of 8,
 // so its part of either bit stream starts on a byte boundary
 constexpr int kDcBits = 11;
