@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kFullThreads) aes_ctr_full_kernel(const __grid
   extern __shared__ __align__(16) uint32_t Trep[];
   for (int i = threadIdx.x; i < kTrepWords; i += kFullThreads) Trep[i] = __ldg(a.T + (i >> 5));
   __syncthreads();
-  const char* Tl = reinterpret_cast<const char*>(Trep) + 4 * (threadIdx.x & 31);
+  const uint32_t Tl = (uint32_t)__cvta_generic_to_shared(Trep) + 4u * (threadIdx.x & 31);
   const uint64_t nfull = a.bytes >> 4;
   const uint64_t stride = (uint64_t)gridDim.x * kFullThreads;
   for (uint64_t i = (uint64_t)blockIdx.x * kFullThreads + threadIdx.x; i < nfull; i += stride) {

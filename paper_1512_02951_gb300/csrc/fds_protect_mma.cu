@@ -237,7 +237,7 @@ __device__ __forceinline__ void pm_work(const PmArgs& a, uint8_t* smem, uint64_t
   const int w = warp - 1 - kPmEpiWarps;
   const int bl = 32 * w + lane;
   const int G = (int)gridDim.x;
-  const char* Tl = reinterpret_cast<const char*>(Ts) + 4 * lane;   // this lane's copy of T0
+  const uint32_t Tl = smem_u32(Ts) + 4u * lane;   // this lane's copy of T0 (shared-window address)
   for (int i = 0; i < nt; ++i) {
     const int s = i % kPmPixSlots;
     if (!mbar_wait_abort(bar + kBarPixFull + s, (i / kPmPixSlots) & 1, abort)) break;

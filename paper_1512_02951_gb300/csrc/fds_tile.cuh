@@ -363,7 +363,7 @@ __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_
 __device__ __forceinline__ void ctr_tile_rep(uint8_t* st, int bytes, uint64_t first_block, const TileSlot* sl,
                                              const uint32_t* rk, const uint32_t* Trep, bool aes_pair = false) {
   const int nblk = (bytes + 15) >> 4;
-  const char* Tl = reinterpret_cast<const char*>(Trep) + 4 * (threadIdx.x & 31);
+  const uint32_t Tl = smem_u32(Trep) + 4u * (threadIdx.x & 31);
   const int step = aes_pair ? 2 * kThreads : kThreads;
   for (int i = threadIdx.x; i < nblk; i += step) {
     const int m_n = aes_pair && i + kThreads < nblk ? 2 : 1;
