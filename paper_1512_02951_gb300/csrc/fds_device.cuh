@@ -296,21 +296,26 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   return v;
 }
 
-// AES-128 with one T-table, T0, replicated 32 times in shared memory: lane L always reads
-// copy L, i.e. bank L, so a warp's 32 lookups never conflict.  Tl = the shared-window address
-// of the table plus 4 * lane (entry x of the lane's copy at Tl + 128 x).  The table index is
+// AES-128 with one T-table, T0, replicated in shared memory: 2^(SH-2) copies, entry x of copy
+// c at word 2^(SH-2) x + c, lane L reading copy L mod 2^(SH-2).  SH = 7 (32 copies, 32 KB):
+// lane L always reads bank L, so a warp's 32 lookups never conflict; SH = 6 (16 copies,
+// 16 KB): lanes L and L + 16 share a copy and meet in a bank at most pairwise.  Tl = the
+// shared-window address of the table plus 4 * (its copy for this lane).  The table index is
 // taken out of the state word by one byte permute and scaled by a shift-add into the address
-// (measured alone: 805 instead of 956 instructions and 8.2 instead of 10.1 SM cycles per
-// block against masking shifted words).  T_r[x] = rotl(T0[x], 8 r) by byte permutes; S[x] is
-// byte 1 of T0[x] (last round).
+// (measured alone, 32 copies: 805 instead of 956 instructions and 8.2 instead of 10.1 SM
+// cycles per block against masking shifted words; 16 copies: 9.8; four separate 1 KB tables,
+// bank conflicts: 14.9).  T_r[x] = rotl(T0[x], 8 r) by byte permutes; S[x] is byte 1 of T0[x]
+// (last round).
+template <int SH>
 __device__ __forceinline__ uint32_t trep_at(uint32_t Tl, uint32_t w, uint32_t sel) {
-  return lds_u32(Tl + (__byte_perm(w, 0u, sel) << 7));
+  return lds_u32(Tl + (__byte_perm(w, 0u, sel) << SH));
 }
+template <int SH = 7>
 __device__ __forceinline__ void aes128_encrypt_rep(uint32_t (&s)[4], const uint32_t* rk, uint32_t Tl) {
-  auto l0 = [&](uint32_t w) { return trep_at(Tl, w, 0x4440u); };
-  auto l1 = [&](uint32_t w) { return trep_at(Tl, w, 0x4441u); };
-  auto l2 = [&](uint32_t w) { return trep_at(Tl, w, 0x4442u); };
-  auto l3 = [&](uint32_t w) { return trep_at(Tl, w, 0x4443u); };
+  auto l0 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4440u); };
+  auto l1 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4441u); };
+  auto l2 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4442u); };
+  auto l3 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4443u); };
   auto r8 = [](uint32_t x) { return __byte_perm(x, x, 0x2103u); };
   auto r16 = [](uint32_t x) { return __byte_perm(x, x, 0x1032u); };
   auto r24 = [](uint32_t x) { return __byte_perm(x, x, 0x0321u); };
@@ -339,12 +344,12 @@ __device__ __forceinline__ void aes128_encrypt_rep(uint32_t (&s)[4], const uint3
 // The same on M independent blocks at once, their rounds interleaved: the M lookups chains
 // overlap, so one warp keeps the table pipe busy where a single block per thread would wait
 // out each round's load latency.
-template <int M>
+template <int M, int SH = 7>
 __device__ __forceinline__ void aes128_encrypt_rep_n(uint32_t (&s)[M][4], const uint32_t* rk, uint32_t Tl) {
-  auto l0 = [&](uint32_t w) { return trep_at(Tl, w, 0x4440u); };
-  auto l1 = [&](uint32_t w) { return trep_at(Tl, w, 0x4441u); };
-  auto l2 = [&](uint32_t w) { return trep_at(Tl, w, 0x4442u); };
-  auto l3 = [&](uint32_t w) { return trep_at(Tl, w, 0x4443u); };
+  auto l0 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4440u); };
+  auto l1 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4441u); };
+  auto l2 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4442u); };
+  auto l3 = [&](uint32_t w) { return trep_at<SH>(Tl, w, 0x4443u); };
   auto r8 = [](uint32_t x) { return __byte_perm(x, x, 0x2103u); };
   auto r16 = [](uint32_t x) { return __byte_perm(x, x, 0x1032u); };
   auto r24 = [](uint32_t x) { return __byte_perm(x, x, 0x0321u); };

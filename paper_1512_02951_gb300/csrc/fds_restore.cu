@@ -112,7 +112,8 @@ __device__ __forceinline__ void decrypt_packed(const TileSlot* sl, uint8_t* land
   uint64_t vo;
   int vb;
   packed_extent<W>(sl, true, vo, vb);
-  ctr_tile_packed(reinterpret_cast<uint32_t*>(land + land_private_offset<W>(sl->k)), vo, vb, sl, rk, Ts);
+  ctr_tile_packed(reinterpret_cast<uint32_t*>(land + land_private_offset<W>(sl->k)), vo, vb, sl, rk, Ts,
+                  (int)threadIdx.x);
 }
 // the landed (decrypted) parts -> int16 staging st, public [cb][63 - k], private [cb][k + 1]
 // (all threads): a public thread unpacks 32 fields (W words), a private thread one
@@ -249,9 +250,9 @@ __device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint
   const int bytes = sl->nb * 6 * (k + 1);
   const uint64_t first = ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4;
   if constexpr (REP)
-    ctr_tile_rep(st + kTileCb * 2 * (63 - k), bytes, first, sl, rk, Ts, aes_pair);
+    ctr_tile_rep(st + kTileCb * 2 * (63 - k), bytes, first, sl, rk, Ts, aes_pair, (int)threadIdx.x);
   else
-    ctr_tile(st + kTileCb * 2 * (63 - k), bytes, first, sl, rk, Ts, aes_pair);
+    ctr_tile(st + kTileCb * 2 * (63 - k), bytes, first, sl, rk, Ts, aes_pair, (int)threadIdx.x);
 }
 
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
@@ -280,10 +281,10 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
   }
   if (t < 4) misc[t] = 0;
   if (t == 0) {
-    misc[4] = next_tile(a, 0);
-    misc[5] = next_tile(a, 1);
+    misc[4] = next_tile(a, 0, blockIdx.x, gridDim.x);
+    misc[5] = next_tile(a, 1, blockIdx.x, gridDim.x);
   }
-  if (t < kTileBlocks) fill_slot(a, blockIdx.x, slot(0));
+  if (t < kTileBlocks) fill_slot(a, blockIdx.x, slot(0), t);
   __syncthreads();
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   uint32_t phase[2] = {0u, 0u};
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
     const int cur = misc[4 + buf], nxt = misc[4 + (buf ^ 1)];
     if (cur >= ntiles) break;
     const TileSlot* sl = slot(it % 3);
-    if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot((it + 1) % 3));
+    if (nxt < ntiles && t < kTileBlocks) fill_slot(a, nxt, slot((it + 1) % 3), t);
     uint8_t* pix = smem + kSmemPix + buf * kPixBytes;
     if (t == 0) {
       misc[0] = 0;
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
       asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
     }
     __syncthreads();                                                       // A
-    if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2) : ntiles;
+    if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2, blockIdx.x, gridDim.x) : ntiles;
     if (nxt < ntiles) {
       if constexpr (PACK != 0)
         load_packed<PACK>(slot((it + 1) % 3), land, bars + (buf ^ 1));

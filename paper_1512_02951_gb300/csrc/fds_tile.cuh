@@ -102,6 +102,8 @@ struct TileArgs {
   int32_t public_image;
   // AES lane schedule of the batched form: nonzero = two keystream blocks per thread
   int32_t aes_pair;
+  // protect: tile groups that work in each CTA (1 .. the kernel's groups; 0 = all of them)
+  int32_t groups;
 };
 
 // What a CTA knows about the tile it is working on (shared memory, filled one tile ahead).
@@ -164,6 +166,12 @@ inline int resident_ctas(Kernel kernel, int threads, int bytes, int (&cache)[kMa
 
 inline int total_tiles(const TileArgs& a) {
   return a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
+}
+
+// barrier of one 192-thread tile group of a CTA (named barrier `id`, never 0: that is the
+// CTA-wide __syncthreads)
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kThreads) : "memory");
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -241,10 +249,9 @@ __device__ __forceinline__ uint64_t block_offset(int width, int gb) {
   return (uint64_t)by * 8ull * (uint64_t)width * 3ull + (uint64_t)bx * 24ull;
 }
 
-// Fill slot s for global tile g.  Called by threads 0 .. kTileBlocks-1 of the CTA (each
-// writes its own fields); the caller publishes the slot with a barrier.
-__device__ __forceinline__ void fill_slot(const TileArgs& a, int g, TileSlot* s) {
-  const int t = threadIdx.x;
+// Fill slot s for global tile g.  Called by threads t = 0 .. kTileBlocks-1 of the tile group
+// (each writes its own fields); the caller publishes the slot with a barrier.
+__device__ __forceinline__ void fill_slot(const TileArgs& a, int g, TileSlot* s, int t) {
   int width, nblocks, k, local;
   uint64_t iv_hi, iv_lo, pxo = 0, puo = 0, pro = 0;
   const uint32_t* rk;
@@ -294,12 +301,13 @@ __device__ __forceinline__ void fill_slot(const TileArgs& a, int g, TileSlot* s)
   if (t < nb) s->blk[t] = block_offset(width, local * kTileBlocks + t);
 }
 
-// Tile schedule of a persistent CTA: the i-th tile is blockIdx.x + i * gridDim.x (static), or
-// for i >= 1 the value of an atomic counter plus gridDim.x (dynamic, a.dispenser non-null;
-// the counter must be zero at launch).  Called by one thread.
-__device__ __forceinline__ int next_tile(const TileArgs& a, int i) {
-  if (a.dispenser == nullptr || i == 0) return blockIdx.x + i * gridDim.x;
-  return (int)atomicAdd(a.dispenser, 1u) + (int)gridDim.x;
+// Tile schedule of a persistent tile group (vb = its index among the launch's vgrid groups;
+// a group is a CTA, or one of the CTA's independent 192-thread groups): the i-th tile is
+// vb + i * vgrid (static), or for i >= 1 the value of an atomic counter plus vgrid (dynamic,
+// a.dispenser non-null; the counter must be zero at launch).  Called by one thread.
+__device__ __forceinline__ int next_tile(const TileArgs& a, int i, int vb, int vgrid) {
+  if (a.dispenser == nullptr || i == 0) return vb + i * vgrid;
+  return (int)atomicAdd(a.dispenser, 1u) + vgrid;
 }
 
 // 24-byte block row of the pixel tile shifted right by `c` bytes: channel c's pixel x is
@@ -321,10 +329,10 @@ __device__ __forceinline__ void load_row_shifted(const uint8_t* tile, int y, int
 // batched form's autotuner can choose), instead of one.
 __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_block,
                                          const TileSlot* sl, const uint32_t* rk, const uint32_t* Ts,
-                                         bool aes_pair = false) {
+                                         bool aes_pair, int t) {
   const int nblk = (bytes + 15) >> 4;
   if (aes_pair) {
-    for (int i = threadIdx.x; i < nblk; i += 2 * kThreads) {
+    for (int i = t; i < nblk; i += 2 * kThreads) {
       const bool two = i + kThreads < nblk;
       uint32_t s[2][4];
       ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s[0]);
@@ -344,7 +352,7 @@ __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_
     }
     return;
   }
-  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+  for (int i = t; i < nblk; i += kThreads) {
     uint32_t s[4];
     ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s);
     aes128_encrypt(s, rk, Ts);
@@ -358,22 +366,24 @@ __device__ __forceinline__ void ctr_tile(uint8_t* st, int bytes, uint64_t first_
   }
 }
 
-// ctr_tile with the lane-replicated T0 table (kTrepWords words at Trep, entry x of copy L at
-// word 32 x + L): every lookup of a warp hits 32 distinct banks.  aes_pair as in ctr_tile.
+// ctr_tile with a replicated T0 table (2^(SH-2) copies at Trep, entry x of copy c at word
+// 2^(SH-2) x + c; SH = 7: every lookup of a warp hits 32 distinct banks).  aes_pair as in
+// ctr_tile; t = the thread's index in its 192-thread tile group.
+template <int SH = 7>
 __device__ __forceinline__ void ctr_tile_rep(uint8_t* st, int bytes, uint64_t first_block, const TileSlot* sl,
-                                             const uint32_t* rk, const uint32_t* Trep, bool aes_pair = false) {
+                                             const uint32_t* rk, const uint32_t* Trep, bool aes_pair, int t) {
   const int nblk = (bytes + 15) >> 4;
-  const uint32_t Tl = smem_u32(Trep) + 4u * (threadIdx.x & 31);
+  const uint32_t Tl = smem_u32(Trep) + 4u * (t & ((1 << (SH - 2)) - 1));
   const int step = aes_pair ? 2 * kThreads : kThreads;
-  for (int i = threadIdx.x; i < nblk; i += step) {
+  for (int i = t; i < nblk; i += step) {
     const int m_n = aes_pair && i + kThreads < nblk ? 2 : 1;
     uint32_t s[2][4];
     ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s[0]);
     if (aes_pair) {
       ctr_block(sl->iv_hi, sl->iv_lo, first_block + i + kThreads, s[1]);
-      aes128_encrypt_rep_n<2>(s, rk, Tl);
+      aes128_encrypt_rep_n<2, SH>(s, rk, Tl);
     } else {
-      aes128_encrypt_rep(s[0], rk, Tl);
+      aes128_encrypt_rep<SH>(s[0], rk, Tl);
     }
     for (int m = 0; m < m_n; ++m) {
       uint4* p = reinterpret_cast<uint4*>(st + 16 * (i + m * kThreads));
@@ -404,16 +414,22 @@ __device__ __forceinline__ void packed_extent(const TileSlot* sl, bool priv, uin
 // AES-128-CTR over the tile's packed private part (words at w, stream bytes [off, off +
 // bytes), off a multiple of 4): one thread per keystream block the part overlaps; a block
 // that straddles two tiles is generated by both, each XORing its own words
+// SH = 0: the four T-tables at Ts, else a replicated T0 as in ctr_tile_rep
+template <int SH = 0>
 __device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int bytes, const TileSlot* sl,
-                                                const uint32_t* rk, const uint32_t* Ts) {
+                                                const uint32_t* rk, const uint32_t* Ts, int t) {
   const uint64_t b0 = off >> 4;
   const int nblk = (int)(((off + (uint64_t)bytes + 15) >> 4) - b0);
   const int nw = (bytes + 3) >> 2;
   const int skew = (int)((off & 15) >> 2);
-  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+  const uint32_t Tl = SH ? smem_u32(Ts) + 4u * (t & ((1 << (SH > 2 ? SH - 2 : 0)) - 1)) : 0u;
+  for (int i = t; i < nblk; i += kThreads) {
     uint32_t s[4];
     ctr_block(sl->iv_hi, sl->iv_lo, b0 + i, s);
-    aes128_encrypt(s, rk, Ts);
+    if constexpr (SH != 0)
+      aes128_encrypt_rep<SH>(s, rk, Tl);
+    else
+      aes128_encrypt(s, rk, Ts);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int wi = 4 * i + m - skew;
