@@ -6,6 +6,7 @@ restore runs in the library's CUDA kernels.  Function names follow include/fds.h
 from __future__ import annotations
 
 import ctypes
+import functools
 import json
 import math
 import os
@@ -33,8 +34,9 @@ def init(device: int = 0) -> None:
     _lib.check(_lib.load().fds_init(device), "fds_init")
 
 
+@functools.lru_cache(maxsize=8192)
 def sizes(width: int, height: int, k: int) -> tuple[int, int]:
-    """fds_sizes: (public bytes, private bytes) of one image."""
+    """fds_sizes: (public bytes, private bytes) of one image (remembered per shape)."""
     pub, priv = ctypes.c_uint64(), ctypes.c_uint64()
     _lib.check(_lib.load().fds_sizes(width, height, k, ctypes.byref(pub), ctypes.byref(priv)),
                "fds_sizes")

@@ -9,16 +9,25 @@ that arrive while other batches are on the GPU are admitted into the next free l
 as memory allows, so work of different batches overlaps on the device.  Keys stay resident
 on the device (key slots); every request names its slot and its own initial counter block.
 
+Host side: inputs that are not pinned host tensors are copied into pinned memory by a pool of
+staging threads when they are submitted (off the scheduler thread); a batch's outputs leave the
+device as one copy per fragment buffer into the lane's pinned host buffers, from which the
+same pool copies each request's result out (the lane takes its next batch once they are
+out).  The lane's device and pinned host buffers persist and grow with the largest batch, so
+a warm server allocates no pinned memory.
+
 Each result is bit-for-bit what the request gives alone: batching changes only which launch
 a request's tiles belong to.
 """
 from __future__ import annotations
 
 import collections
+import functools
+import os
 import queue
 import threading
 import time
-from concurrent.futures import Future
+from concurrent.futures import Future, ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -42,10 +51,21 @@ class Request:
     done: float = 0.0              # time.perf_counter() when the result was ready
     future: Future = field(default_factory=Future)
 
+    _sizes: tuple = None           # (pixel, public, private) bytes, computed once
+    _staged: tuple = None          # pinned host copies of the inputs (the inputs stay as given)
+
+    def inputs(self) -> tuple:
+        """The inputs the lane copies to the device: the staged copies once there are some."""
+        if self._staged is not None:
+            return self._staged
+        return (self.pixels,) if self.kind == "protect" else (self.public, self.private)
+
     def sizes(self):
-        from . import api
-        pub, priv = api.sizes(self.width, self.height, self.k)
-        return self.width * self.height * 3, pub, priv
+        if self._sizes is None:
+            from . import api
+            pub, priv = api.sizes(self.width, self.height, self.k)
+            self._sizes = (self.width * self.height * 3, pub, priv)
+        return self._sizes
 
     def device_bytes(self) -> int:
         px, pub, priv = self.sizes()
@@ -53,7 +73,12 @@ class Request:
 
 
 class GpuLane:
-    """One CUDA stream and a reusable plan; runs one batch at a time."""
+    """One CUDA stream, a reusable plan, and device and pinned host buffers that grow with the
+    largest batch; runs one batch at a time.
+
+    Life of a batch: launch() (copies in, one batched launch, copies out, on the stream);
+    done() once the stream has passed it; finish() hands back one result builder per request
+    (each copies its result out of the pinned buffers); release() once all have run."""
 
     def __init__(self, device, capacity):
         import torch
@@ -64,15 +89,26 @@ class GpuLane:
         self.stream = torch.cuda.Stream(device)
         with torch.cuda.device(device):
             self.plan = api.Plan(capacity=capacity)
+        self.bufs = [None, None, None]       # pixels, public, private (device, uint8)
+        self.hbufs = [None, None]            # outputs (pinned host, uint8)
         self.event = None
         self.batch = None
         self.hold = None
+        self.draining = False
 
     def busy(self) -> bool:
         return self.batch is not None
 
     def done(self) -> bool:
-        return self.batch is not None and self.event.query()
+        return self.batch is not None and not self.draining and self.event.query()
+
+    def _grow(self, bufs, i: int, n: int, **kw):
+        b = bufs[i]
+        if b is None or b.numel() < n:
+            # this lane's previous batch is over (the lane was free), so the old buffer may go
+            b = self.torch.empty(max(n, 16, 2 * (b.numel() if b is not None else 0)), dtype=self.torch.uint8, **kw)
+            bufs[i] = b
+        return b
 
     def launch(self, batch: list[Request]) -> None:
         torch, api = self.torch, self.api
@@ -80,62 +116,79 @@ class GpuLane:
         descs = [api.ImageDesc(r.width, r.height, r.k, r.key_slot, r.iv) for r in batch]
         npx, npub, npriv = api.layout(descs)
         with torch.cuda.stream(self.stream):
-            px = torch.empty(max(npx, 16), dtype=torch.uint8, device=self.device)
-            pub = torch.empty(max(npub, 16), dtype=torch.uint8, device=self.device)
-            priv = torch.empty(max(npriv, 16), dtype=torch.uint8, device=self.device)
-            outs = []
+            dev = dict(device=self.device)
+            px, pub, priv = (self._grow(self.bufs, 0, npx, **dev), self._grow(self.bufs, 1, npub, **dev),
+                             self._grow(self.bufs, 2, npriv, **dev))
             for r, d in zip(batch, descs):
                 n, pb, vb = r.sizes()
+                ins = r.inputs()
                 if kind == "protect":
-                    px[d.pixel_offset: d.pixel_offset + n].copy_(_as_u8(torch, r.pixels), non_blocking=True)
+                    px[d.pixel_offset: d.pixel_offset + n].copy_(_host_u8(torch, ins[0]), non_blocking=True)
                 else:
-                    pub[d.public_offset: d.public_offset + pb].copy_(_as_u8(torch, r.public), non_blocking=True)
-                    priv[d.private_offset: d.private_offset + vb].copy_(_as_u8(torch, r.private), non_blocking=True)
+                    pub[d.public_offset: d.public_offset + pb].copy_(_host_u8(torch, ins[0]), non_blocking=True)
+                    priv[d.private_offset: d.private_offset + vb].copy_(_host_u8(torch, ins[1]), non_blocking=True)
             self.plan.update(descs, self.stream)
             if kind == "protect":
                 self.plan.protect(px, pub, priv)
+                h0 = self._grow(self.hbufs, 0, npub, pin_memory=True)
+                h1 = self._grow(self.hbufs, 1, npriv, pin_memory=True)
+                h0[:npub].copy_(pub[:npub], non_blocking=True)
+                h1[:npriv].copy_(priv[:npriv], non_blocking=True)
             else:
                 self.plan.restore(pub, priv, px)
-            for r, d in zip(batch, descs):
-                n, pb, vb = r.sizes()
-                if kind == "protect":
-                    hp = torch.empty(pb, dtype=torch.uint8, pin_memory=True)
-                    hv = torch.empty(vb, dtype=torch.uint8, pin_memory=True)
-                    hp.copy_(pub[d.public_offset: d.public_offset + pb], non_blocking=True)
-                    hv.copy_(priv[d.private_offset: d.private_offset + vb], non_blocking=True)
-                    outs.append((hp, hv))
-                else:
-                    hx = torch.empty(n, dtype=torch.uint8, pin_memory=True)
-                    hx.copy_(px[d.pixel_offset: d.pixel_offset + n], non_blocking=True)
-                    outs.append(hx)
+                h0 = self._grow(self.hbufs, 0, npx, pin_memory=True)
+                h0[:npx].copy_(px[:npx], non_blocking=True)
             self.event = torch.cuda.Event()
             self.event.record(self.stream)
-        self.batch, self.hold = batch, (px, pub, priv, outs)
+        self.batch, self.hold = batch, descs
 
     def finish(self) -> list[tuple[Request, object]]:
-        """Results of the finished batch: protect -> (public int16 array [H/8, W/8, 3, 63-k],
-        private bytes); restore -> H x W x 3 uint8 array."""
-        batch, (_, _, _, outs) = self.batch, self.hold
-        res = []
-        for r, o in zip(batch, outs):
-            if r.kind == "protect":
-                pub = o[0].numpy().view(np.int16).reshape(r.height // 8, r.width // 8, 3, 63 - r.k)
-                res.append((r, (pub, o[1].numpy().tobytes())))
-            else:
-                res.append((r, o.numpy().reshape(r.height, r.width, 3)))
+        """One (request, builder) per request of the finished batch; builder() returns the
+        result copied out of the pinned buffers: protect -> (public int16 array
+        [H/8, W/8, 3, 63-k], private bytes); restore -> H x W x 3 uint8 array.  Call release()
+        after every builder has run."""
+        self.draining = True
+        host = [h.numpy() if h is not None else None for h in self.hbufs]
+        out = []
+        for r, d in zip(self.batch, self.hold):
+            out.append((r, functools.partial(_result_of, r, d, host)))
+        return out
+
+    def release(self) -> None:
         self.batch = self.hold = self.event = None
-        return res
+        self.draining = False
 
     def close(self) -> None:
         self.plan.close()
 
 
-def _as_u8(torch, a):
+def _result_of(r: Request, d, host):
+    """Request r's result copied out of the lane's pinned host buffers `host` (numpy views)."""
+    n, pb, vb = r.sizes()
+    if r.kind == "protect":
+        pub = np.array(host[0][d.public_offset: d.public_offset + pb]).view(np.int16).reshape(
+            r.height // 8, r.width // 8, 3, 63 - r.k)
+        return pub, host[1][d.private_offset: d.private_offset + vb].tobytes()
+    return np.array(host[0][d.pixel_offset: d.pixel_offset + n]).reshape(r.height, r.width, 3)
+
+
+def _host_u8(torch, a):
+    """A request input as a flat uint8 host tensor (pinned once staged)."""
     if isinstance(a, torch.Tensor):
         return a.reshape(-1).view(torch.uint8)
     if isinstance(a, (bytes, bytearray)):
         return torch.frombuffer(bytearray(a), dtype=torch.uint8)
     return torch.from_numpy(np.ascontiguousarray(a).reshape(-1).view(np.uint8))
+
+
+def _stage(torch, a):
+    """A pinned host copy of input `a` (itself if it already is a pinned CPU tensor)."""
+    if isinstance(a, torch.Tensor) and (a.is_cuda or a.is_pinned()):
+        return a
+    src = _host_u8(torch, a)
+    dst = torch.empty(src.numel(), dtype=torch.uint8, pin_memory=True)
+    dst.copy_(src)
+    return dst
 
 
 class Server:
@@ -144,12 +197,20 @@ class Server:
     lanes: batches in flight at once (each on its own stream); max_batch: requests per batch;
     mem_budget: device bytes that admitted requests may hold at once (default: half of the
     device memory free at start).  A request larger than the whole budget is rejected.
-    ``lane_factory(i)`` builds a lane (GpuLane by default; tests pass CPU fakes)."""
+    ``lane_factory(i)`` builds a lane (GpuLane by default; tests pass CPU fakes).
+    stage_threads: threads that copy inputs which are not pinned host tensors into pinned
+    memory before they join the queue (GPU lanes only; 0 = the scheduler copies from pageable
+    memory itself)."""
 
     def __init__(self, device: int = 0, lanes: int = 3, max_batch: int = 64,
-                 mem_budget: int | None = None, lane_factory=None):
+                 mem_budget: int | None = None, lane_factory=None, stage_threads: int | None = None):
         self.max_batch = max_batch
+        self._stager = None
         if lane_factory is None:
+            if stage_threads is None:
+                stage_threads = min(8, os.cpu_count() or 1)
+            if stage_threads > 0:
+                self._stager = ThreadPoolExecutor(max_workers=stage_threads, thread_name_prefix="fds-stage")
             import torch
 
             from . import api
@@ -164,6 +225,8 @@ class Server:
         self.ready: collections.deque = collections.deque()
         self.in_use = 0                 # device bytes of admitted, unfinished requests
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "max_lanes_busy": 0}
+        self._pending = 0               # requests still being staged
+        self._lock = threading.Lock()
         self._stop = False
         self._thread = threading.Thread(target=self._loop, name="fds-serve", daemon=True)
         self._thread.start()
@@ -174,12 +237,37 @@ class Server:
         if req.device_bytes() > self.mem_budget:
             raise ValueError("request larger than the server's device-memory budget")
         req.arrival = time.perf_counter()
-        self.inbox.put(req)
+        if self._stager is not None and not self._pinned(req):
+            with self._lock:
+                self._pending += 1
+            self._stager.submit(self._stage_then_queue, req)
+        else:
+            self.inbox.put(req)
         return req.future
+
+    @staticmethod
+    def _pinned(req: Request) -> bool:
+        import torch
+        return all(isinstance(a, torch.Tensor) and (a.is_cuda or a.is_pinned()) for a in req.inputs())
+
+    def _stage_then_queue(self, req: Request) -> None:
+        import torch
+        try:
+            req._staged = tuple(_stage(torch, a) for a in req.inputs())
+        except BaseException as exc:                          # the request fails, not the server
+            req.future.set_exception(exc)
+            with self._lock:
+                self._pending -= 1
+            return
+        self.inbox.put(req)
+        with self._lock:
+            self._pending -= 1
 
     def close(self) -> None:
         self._stop = True
         self._thread.join()
+        if self._stager is not None:
+            self._stager.shutdown(wait=True)
         for lane in self.lanes:
             if hasattr(lane, "close"):
                 lane.close()
@@ -191,11 +279,7 @@ class Server:
                 progressed = False
                 for lane in self.lanes:                       # retire finished batches
                     if lane.busy() and lane.done():
-                        now = time.perf_counter()
-                        for r, res in lane.finish():
-                            self.in_use -= r.device_bytes()
-                            r.done = now
-                            r.future.set_result(res)
+                        self._retire(lane)
                         progressed = True
                 while True:                                   # arrivals join the ready list
                     try:
@@ -215,7 +299,7 @@ class Server:
                     progressed = True
                 busy = sum(lane.busy() for lane in self.lanes)
                 self.stats["max_lanes_busy"] = max(self.stats["max_lanes_busy"], busy)
-                if self._stop and not self.ready and busy == 0 and self.inbox.empty():
+                if self._stop and not self.ready and busy == 0 and self.inbox.empty() and self._pending == 0:
                     return
                 if not progressed:
                     if busy:
@@ -234,6 +318,51 @@ class Server:
                     if not r.future.done():
                         r.future.set_exception(exc)
             raise
+
+    def _retire(self, lane) -> None:
+        """A batch the GPU has finished: its device memory is free; its results are delivered
+        (copied out by the staging pool when they come as builders), then the lane is free."""
+        parts = lane.finish()
+        for r, _ in parts:
+            self.in_use -= r.device_bytes()
+        deferred = [(r, res) for r, res in parts if callable(res)]
+        now = time.perf_counter()
+        for r, res in parts:
+            if not callable(res):
+                r.done = now
+                r.future.set_result(res)
+        if not deferred:
+            if hasattr(lane, "release"):
+                lane.release()
+            return
+        if self._stager is None:
+            for r, fn in deferred:
+                self._deliver(r, fn)
+            lane.release()
+            return
+        left = [len(deferred)]
+
+        def run(r, fn):
+            self._deliver(r, fn)
+            with self._lock:
+                left[0] -= 1
+                last = left[0] == 0
+            if last:
+                lane.release()
+
+        for r, fn in deferred:
+            self._stager.submit(run, r, fn)
+
+    @staticmethod
+    def _deliver(r: Request, fn) -> None:
+        try:
+            res = fn()
+        except BaseException as exc:
+            r.done = time.perf_counter()
+            r.future.set_exception(exc)
+            return
+        r.done = time.perf_counter()
+        r.future.set_result(res)
 
     def _take_batch(self) -> list[Request]:
         """Oldest ready request's kind; then every ready request of that kind, in arrival
