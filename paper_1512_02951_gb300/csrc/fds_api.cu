@@ -1646,7 +1646,7 @@ int fds_plan_update(fds_plan* plan, const fds_image* images, int32_t n, void* st
 int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic, int32_t largest_first) {
   if (!plan) return set_err(FDS_E_INVALID, "null plan");
   if (ctas_per_sm < 0 || ctas_per_sm > FDS_PROTECT_MAX_CTAS_PER_SM)
-    return set_err(FDS_E_INVALID, "ctas_per_sm must be 0 .. 4");
+    return set_err(FDS_E_INVALID, "ctas_per_sm must be 0 .. " + std::to_string(FDS_PROTECT_MAX_CTAS_PER_SM));
   int rc = plan_device(plan);
   if (rc) return rc;
   for (int dir = 0; dir < 2; ++dir) {

@@ -129,7 +129,7 @@ def test_plan_direction_schedules_and_aes_lane_pairs(api, ks):
     descs, imgs, keys, px, npub, npriv = _batch(api, SIZES, ks, seed=23)
     want = _per_image(api, descs, px, npub, npriv)
     plan = api.Plan(descs)
-    for ps, rs in ((1, 1), (2, 2), (3, 1), (4, 2), (0, 0)):
+    for ps, rs in ((1, 1), (2, 2), (3, 1), (3, 2), (0, 0)):
         for dyn in (0, 1):
             for aes in (0, 1):
                 plan.set_direction_schedule("protect", ps, bool(dyn), bool(aes))
@@ -139,6 +139,8 @@ def test_plan_direction_schedules_and_aes_lane_pairs(api, ks):
     from paper_1512_02951_gb300 import _lib
     with pytest.raises(_lib.FdsError):
         plan.set_direction_schedule("restore", 3)
+    with pytest.raises(_lib.FdsError):
+        plan.set_direction_schedule("protect", 4)
     plan.close()
     for d in descs:
         api.key_release(d.key_slot)
