@@ -268,12 +268,14 @@ int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
 #define FDS_TC_F16 2
 #define FDS_TC_F16_K_LIST "0, 5"
 /* FDS_TC_F16 is the warp-specialised form: one persistent CTA per SM, tiles of 128 pixel
- * blocks; a producer warp moves pixel rows in with bulk copies, one thread issues the MMAs
- * (D = A B^T per channel, A = p - 128 in f16, B = the basis with rows in zigzag order split
- * as (L0 + L1 2^-11 + L2 2^-22) 2^-13, |L| <= 2048, so the FP32 accumulators are exact integer
- * sums; the integer part is rounded from limb 0 alone and limbs 1, 2 only form the residual),
- * sixteen warps de-interleave the pixels and round the accumulators (one thread per pixel
- * block, four warps per block covering its three channels), and four warps generate the CTR keystream ahead of use.  The error of
+ * blocks, thirteen warps.  A control warp moves pixel rows in with bulk copies and, from one
+ * elected thread, issues the MMAs (D = A B^T per channel, A = p - 128 in f16, B = the basis
+ * with rows in zigzag order split as (L0 + L1 2^-11 + L2 2^-22) 2^-13, |L| <= 2048, so the
+ * FP32 accumulators are exact integer sums; the integer part is rounded from limb 0 alone and
+ * limbs 1, 2 only form the residual); four work warps de-interleave the pixels into the A
+ * operands and generate the CTR keystream ahead of use; eight epilogue warps (two per TMEM
+ * lane quadrant, one thread per pixel block) round the accumulators and write the fragments.
+ * The error of
  * a coefficient before rounding is below the bound fds_tc_basis reports (about 6e-5, and about
  * 1e-7 + |F| 2^-24 for a value F); values
  * within it of a half-integer are re-decided exactly.  Selections k in FDS_TC_F16_K_LIST,

@@ -2,7 +2,7 @@
 
   * the 4096 x 4096 RGB image (the benchmark workload) at k = 0 and k = 5: every public int16,
     every ciphertext byte and every restored pixel, for the float32 CUDA-core kernels and for
-    both tensor-core forms of protect;
+    the three tensor-core forms of protect;
   * the per-block float32 error guard of the protect kernel, u (2.7 V + 0.9 W + 1), on every
     channel-block of that image and of a 200-image batch of uneven sizes;
   * the batched plan (one persistent launch per direction over a 2000-image batch of uneven
@@ -69,7 +69,7 @@ def test_4096_whole_image_bit_exact(api, k):
     assert 0.88 < np.mean(back_h == img) < 0.97
 
 
-@pytest.mark.parametrize("form", ["bf16", "tf32"])
+@pytest.mark.parametrize("form", ["bf16", "tf32", "f16"])
 @pytest.mark.parametrize("k", [0, 5])
 def test_4096_whole_image_tensor_core_forms_bit_exact(api, form, k):
     img, key, iv, want_pub, want_priv, _ = _oracle(k)
