@@ -138,19 +138,20 @@ int fds_plan_reserve(int32_t capacity, fds_plan** plan_out);
  * after it).  Waits only for the previous update's copy to have left the staging area. */
 int fds_plan_update(fds_plan* plan, const fds_image* images, int32_t n, void* stream);
 
-/* The most a schedule may launch per SM: protect runs one CTA per SM holding up to three
- * independent tile groups of 192 threads (its "ctas_per_sm" counts those groups); restore
- * runs up to two CTAs of 192 threads per SM. */
-#define FDS_PROTECT_MAX_CTAS_PER_SM 3
+/* The most a plan's schedule may launch per SM: protect runs one CTA per SM holding up to
+ * four independent tile groups of 192 threads (its "ctas_per_sm" counts those groups; one
+ * image outside a plan runs three, which share one AES table); restore runs up to two CTAs
+ * of 192 threads per SM. */
+#define FDS_PROTECT_MAX_CTAS_PER_SM 4
 #define FDS_RESTORE_MAX_CTAS_PER_SM 2
 
 /* Schedule of the persistent launches, both directions at once.  ctas_per_sm: tile groups
- * (protect) or CTAs (restore) per SM, 0 = the most (protect 3, restore 2), 1 .. 3 (restore
- * takes 3 as 0); dynamic: 0 = static round-robin tile assignment, 1 = tiles handed
+ * (protect) or CTAs (restore) per SM, 0 = the most (protect 4, restore 2), 1 .. 4 (restore
+ * takes values above 2 as 0); dynamic: 0 = static round-robin tile assignment, 1 = tiles handed
  * out by an atomic counter; largest_first: 0 = tiles in descriptor order, 1 = images by
  * decreasing size (shared by the directions).  The lane schedule of both directions goes
  * back to one keystream block per thread.  Re-uploads the tile order when it changes and
- * drops captured graphs.  FDS_E_INVALID for ctas_per_sm outside 0 .. 3. */
+ * drops captured graphs.  FDS_E_INVALID for ctas_per_sm outside 0 .. 4. */
 int fds_plan_set_schedule(fds_plan* plan, int32_t ctas_per_sm, int32_t dynamic,
                           int32_t largest_first);
 
@@ -170,7 +171,7 @@ int fds_plan_set_direction_schedule(fds_plan* plan, int32_t direction, int32_t c
 int fds_plan_get_direction_schedule(const fds_plan* plan, int32_t direction,
                                     int32_t* ctas_per_sm, int32_t* dynamic, int32_t* aes_pair);
 
-/* Time every protect schedule on this batch (tile order x ctas_per_sm 1 .. 3 x dynamic x
+/* Time every protect schedule on this batch (tile order x ctas_per_sm 1 .. 4 x dynamic x
  * aes_pair, `reps` launches each after one warm-up, on `stream`) and keep the fastest.  The
  * buffers are written to; their previous contents are lost.  Synchronises the device. */
 int fds_plan_autotune(fds_plan* plan, const uint8_t* pixels, int16_t* public_out,

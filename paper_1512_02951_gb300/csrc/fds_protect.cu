@@ -44,7 +44,6 @@
 
 namespace fds {
 
-constexpr int kPGroups = 3;                                  // tile groups per CTA, one CTA per SM
 // one group's area
 constexpr int kSmemPix = 0;                                  // 2 pixel tiles
 constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 1 staging area
@@ -54,10 +53,20 @@ constexpr int kSmemSlot = kSmemQueue + 8 * kDeferCap;        // 3 tile slots (ri
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
 constexpr int kGroupBytes = kSmemMisc + 32;
-// the CTA: the groups' areas, then the AES table (T0 replicated per lane)
-constexpr int kSmemT = kPGroups * kGroupBytes;
-constexpr int kSmemBytes = kSmemT + 4 * kTrepWords;
-static_assert(kGroupBytes % 16 == 0 && kSmemBytes <= 227 * 1024, "protect shared memory");
+// One image: one CTA per SM of three groups, then the AES table they share (T0 replicated
+// per lane).  Batches: up to four CTAs per SM of one group each, with the four 1 KB T-tables
+// after its area (a batch's tiles mostly carry little keystream -- k = 0: 24 blocks a tile).
+template <bool BATCH>
+struct PLayout {
+  static constexpr int kGroups = BATCH ? 1 : 3;
+  static constexpr int kCtasPerSm = BATCH ? 4 : 1;
+  static constexpr bool kSharedT = !BATCH;
+  static constexpr int kGroupStride = kGroupBytes + (kSharedT ? 0 : 4096);
+  static constexpr int kT = kSharedT ? kGroups * kGroupStride : kGroupBytes;   // CTA / group offset
+  static constexpr int kBytes = kGroups * kGroupStride + (kSharedT ? 4 * kTrepWords : 0);
+};
+static_assert(kGroupBytes % 16 == 0 && PLayout<false>::kBytes <= 227 * 1024 && PLayout<true>::kBytes <= 227 * 1024,
+              "protect shared memory");
 
 // the public / private fragment staged for slot sl (staging area st) to global memory, one
 // bulk group each; one thread
@@ -308,10 +317,18 @@ __host__ __device__ constexpr int pair_col(int j, int l) {
 // from the kernel parameters, which AES then takes as constant-bank operands).
 // PACK: 0 = int16 fragments; 11 or 8 = packed streams (one image)
 template <int K, bool DEBUG, bool BATCH, int PACK = 0>
-__global__ void __launch_bounds__(kThreads * kPGroups, 1) protect_kernel(const __grid_constant__ TileArgs a) {
+__global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BATCH>::kCtasPerSm)
+    protect_kernel(const __grid_constant__ TileArgs a) {
+  using L = PLayout<BATCH>;
+  constexpr int kPGroups = L::kGroups;
   extern __shared__ __align__(128) uint8_t smem_cta[];
-  uint32_t* Ts = reinterpret_cast<uint32_t*>(smem_cta + kSmemT);   // T0 replicated per lane, shared
-  for (int i = threadIdx.x; i < kTrepWords; i += kThreads * kPGroups) Ts[i] = __ldg(a.T + (i >> 5));
+  if constexpr (L::kSharedT) {   // T0 replicated per lane, shared by the groups
+    uint32_t* T = reinterpret_cast<uint32_t*>(smem_cta + L::kT);
+    for (int i = threadIdx.x; i < kTrepWords; i += kThreads * kPGroups) T[i] = __ldg(a.T + (i >> 5));
+  } else {                       // each group's four T-tables
+    for (int i = threadIdx.x; i < kPGroups * 1024; i += kThreads * kPGroups)
+      reinterpret_cast<uint32_t*>(smem_cta + (i >> 10) * L::kGroupStride + L::kT)[i & 1023] = a.T[i & 1023];
+  }
   __syncthreads();
   // this thread's tile group: index, thread index in it, place among all groups of the launch
   const int grp = (int)threadIdx.x / kThreads;
@@ -320,7 +337,8 @@ __global__ void __launch_bounds__(kThreads * kPGroups, 1) protect_kernel(const _
   if (grp >= ng) return;
   const int vb = (int)blockIdx.x * ng + grp, vgrid = (int)gridDim.x * ng;
   const int gbar = 1 + grp;
-  uint8_t* smem = smem_cta + grp * kGroupBytes;
+  uint8_t* smem = smem_cta + grp * L::kGroupStride;
+  const uint32_t* Ts = reinterpret_cast<const uint32_t*>(L::kSharedT ? smem_cta + L::kT : smem + L::kT);
   uint2* deferred = reinterpret_cast<uint2*>(smem + kSmemQueue);   // near ties, after the tile loop
   // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
   int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
@@ -527,13 +545,17 @@ __global__ void __launch_bounds__(kThreads * kPGroups, 1) protect_kernel(const _
       uint64_t off;
       int bytes;
       packed_extent<PACK>(sl, true, off, bytes);
-      ctr_tile_packed<7>(reinterpret_cast<uint32_t*>(privst), off, bytes, sl, a.rk, Ts, t);
+      ctr_tile_packed<L::kSharedT ? 7 : 0>(reinterpret_cast<uint32_t*>(privst), off, bytes, sl, a.rk, Ts, t);
     } else {
       if (t == 0) store_public(sl, smem + kSmemStage);   // final: it leaves during the AES
       if (!a.plain_private)
-        ctr_tile_rep<7>(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1),
-                        ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4, sl,
-                        BATCH ? sl->rk : a.rk, Ts, BATCH && a.aes_pair, t);
+      {
+        const uint64_t first = ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4;
+        if constexpr (L::kSharedT)
+          ctr_tile_rep<7>(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1), first, sl, a.rk, Ts, false, t);
+        else
+          ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1), first, sl, sl->rk, Ts, a.aes_pair, t);
+      }
     }
     fence_proxy_async();
     have_prev = true;
@@ -582,15 +604,18 @@ __global__ void __launch_bounds__(kThreads * kPGroups, 1) protect_kernel(const _
 template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
-  cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, kSmemBytes, attr);
+  using L = PLayout<BATCH>;
+  cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, L::kBytes, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
-  // per_sm: tile groups working on each SM (one CTA per SM)
+  // per_sm: tile groups working on each SM (one image: groups of the one CTA; batches: CTAs)
   TileArgs b = a;
-  b.groups = per_sm >= 1 && per_sm < kPGroups ? per_sm : kPGroups;
+  const int want = per_sm >= 1 && per_sm < L::kGroups * L::kCtasPerSm ? per_sm : L::kGroups * L::kCtasPerSm;
+  b.groups = want < L::kGroups ? want : L::kGroups;
   const int need = (ntiles + b.groups - 1) / b.groups;
-  const int grid = need < sms ? need : sms;
-  if (grid > 0) protect_kernel<K, DEBUG, BATCH, PACK><<<grid, kThreads * kPGroups, kSmemBytes, s>>>(b);
+  const int cap = sms * (want / b.groups);
+  const int grid = need < cap ? need : cap;
+  if (grid > 0) protect_kernel<K, DEBUG, BATCH, PACK><<<grid, kThreads * L::kGroups, L::kBytes, s>>>(b);
   return cudaGetLastError();
 }
 

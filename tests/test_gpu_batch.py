@@ -112,7 +112,7 @@ def test_plan_graph_replay_and_autotune(api):
     pub = torch.empty(npub, dtype=torch.uint8, device=DEV)
     priv = torch.empty(npriv, dtype=torch.uint8, device=DEV)
     ps, dyn, lf = plan.autotune(px, pub, priv, reps=2)
-    assert 1 <= ps <= 3 and dyn in (0, 1) and lf in (0, 1)
+    assert 1 <= ps <= 4 and dyn in (0, 1) and lf in (0, 1)
     _same(descs, want, _plan_run(plan, px, npub, npriv, graph=True, bufs=bufs))
     _same(descs, want, _plan_run(plan, px, npub, npriv, graph=False))
     plan.close()
@@ -129,7 +129,7 @@ def test_plan_direction_schedules_and_aes_lane_pairs(api, ks):
     descs, imgs, keys, px, npub, npriv = _batch(api, SIZES, ks, seed=23)
     want = _per_image(api, descs, px, npub, npriv)
     plan = api.Plan(descs)
-    for ps, rs in ((1, 1), (2, 2), (3, 1), (3, 2), (0, 0)):
+    for ps, rs in ((1, 1), (2, 2), (3, 1), (4, 2), (0, 0)):
         for dyn in (0, 1):
             for aes in (0, 1):
                 plan.set_direction_schedule("protect", ps, bool(dyn), bool(aes))
@@ -140,7 +140,7 @@ def test_plan_direction_schedules_and_aes_lane_pairs(api, ks):
     with pytest.raises(_lib.FdsError):
         plan.set_direction_schedule("restore", 3)
     with pytest.raises(_lib.FdsError):
-        plan.set_direction_schedule("protect", 4)
+        plan.set_direction_schedule("protect", 5)
     plan.close()
     for d in descs:
         api.key_release(d.key_slot)
@@ -159,7 +159,7 @@ def test_plan_tunes_both_directions_and_caches_the_choice(api, tmp_path):
     got = plan.tune(px, *bufs, reps=2, cache=cache)
     assert got["cached"] is False
     cands = got["candidates"]
-    assert len(cands) == 2 * (3 * 2 * 2 + 2 * 2 * 2)        # tile orders x protect + restore grids
+    assert len(cands) == 2 * (4 * 2 * 2 + 2 * 2 * 2)        # tile orders x protect + restore grids
     assert all(c["ms"] > 0 for c in cands)
     for d in ("protect", "restore"):                         # the kept schedule is the fastest
         best = min((c for c in cands if c["direction"] == d and c["largest_first"] == got["largest_first"]),
