@@ -645,17 +645,27 @@ def precision_arm(args):
                      "bit_identical_to_f32_path": bool(torch.equal(frags[0], first[0]) and
                                                        torch.equal(frags[1], first[1]))}
     api.protect_image(img, key, iv, K_SEL, pub, priv)
-    rms = _median_launch_ms(lambda: api.restore_image(pub, priv, WIDTH, HEIGHT, K_SEL, key, iv, out),
-                            args, flush, stream)
-    rgbs = alg_bytes / (rms * 1e-3) / 1e9
-    restore = {"f32_cuda_cores": {"restore_ms": round(rms, 5), "achieved_gbs": round(rgbs, 1),
-                                  "frac": round(rgbs / peak, 4)},
-               "tensor_core_inverse": "not built: the inverse transform stays on the float32 CUDA cores "
-                                      "(exact by the same guard); its int16 coefficient operand needs a hi/lo "
-                                      "split (six limb products instead of three), and the per-pixel epilogue "
-                                      "that stays costs as much as the butterflies it would remove: the forward "
-                                      "forms, whose pixel operand needs no split, at best match the float32 kernel"}
+    restore = {}
+    rforms = {"f32_cuda_cores": lambda: api.restore_image(pub, priv, WIDTH, HEIGHT, K_SEL, key, iv, out),
+              "f16_3limb_tcgen05_inverse": lambda: api.restore_image_tc(pub, priv, WIDTH, HEIGHT, K_SEL, key, iv, out)}
+    rfirst = None
+    for name, fn in rforms.items():
+        api.counters(reset=True)
+        out.fill_(0)
+        fn()
+        torch.cuda.synchronize()
+        slow, esc, fails = api.counters()
+        got = out.clone()
+        if rfirst is None:
+            rfirst = got
+        rms = _median_launch_ms(fn, args, flush, stream)
+        rgbs = alg_bytes / (rms * 1e-3) / 1e9
+        restore[name] = {"restore_ms": round(rms, 5), "achieved_gbs": round(rgbs, 1), "frac": round(rgbs / peak, 4),
+                         "slow_path_values": slow, "escalations_256bit": esc, "failures": fails,
+                         "exact_restore_fraction": round((got == img).to(torch.float64).mean().item(), 6),
+                         "bit_identical_to_f32_path": bool(torch.equal(got, rfirst))}
     bounds = {f: api.tc_basis(f)[1] for f in ("bf16", "tf32", "f16")}
+    bounds["f16_inverse_per_unit_sum_abs_q"] = api.tc_basis("f16_inverse")[1]
     best = max(res.values(), key=lambda r: r["achieved_gbs"])
     # the headline: the fastest tensor-core form
     tc_name = min((n for n in res if n != "f32_cuda_cores"), key=lambda n: res[n]["protect_ms"])
@@ -672,7 +682,7 @@ def precision_arm(args):
             "forms": res, "restore": restore, "proven_error_bounds": bounds,
             "roofline": {"bound": "hbm", "achieved": best["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": best["frac"], "traffic": None},
-            "gpu_launches": args.steps * (len(forms) + 1)}
+            "gpu_launches": args.steps * (len(forms) + len(rforms))}
     emit(line)
 
 

@@ -268,6 +268,8 @@ int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
 #define FDS_TC_TF32 1
 #define FDS_TC_F16 2
 #define FDS_TC_F16_K_LIST "0, 5"
+/* the inverse transform's table, for fds_tc_basis only */
+#define FDS_TC_F16_INVERSE 3
 /* FDS_TC_F16 is the warp-specialised form: one persistent CTA per SM, tiles of 128 pixel
  * blocks, thirteen warps.  A control warp moves pixel rows in with bulk copies and, from one
  * elected thread, issues the MMAs (D = A B^T per channel, A = p - 128 in f16, B = the basis
@@ -284,6 +286,25 @@ int fds_debug_dct_f32(const uint8_t* pixels, int32_t width, int32_t height,
 int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int32_t height,
                          int32_t k, const uint8_t key[16], const uint8_t iv[16],
                          int16_t* public_out, uint8_t* private_out, void* stream);
+
+/* Restore with the inverse 8x8 transform on tensor cores (Sect. 3.2, Fig. 3; the separable
+ * transform of Sect. 6.4.2 as a matrix product; form FDS_TC_F16 only, else FDS_E_INVALID).
+ * Per tile of 64 pixel blocks (192 channel-blocks), D = A B^T as tcgen05 MMAs: A = each
+ * channel-block's 64 coefficients in zigzag order in f16 (exact, since |q| < 2048), B = the
+ * inverse basis, row 8y + x of limb l of 2^9 b_u(y) b_v(x) in zigzag column order, split as
+ * L0 + L1 2^-8 + L2 2^-16 with |L| <= 128, so every product and partial sum is an integer
+ * below 2^24 and the FP32 accumulators are exact.  A pixel is (D0 + D1 2^-8 + D2 2^-16) 2^-9
+ * within S 2^-24 of its exact value (S = sum |q| of its channel-block; fds_tc_basis with
+ * FDS_TC_F16_INVERSE reports the proven bound per unit of S); values within S 2^-24 + 2^-22 of a
+ * half-integer are re-decided exactly from integer coordinates in Z[cos(pi/16)], so the
+ * output equals fds_restore_image's byte for byte for any int16 fragments.  A tile holding a
+ * coefficient of magnitude 2048 or more is inverted by the float32 butterflies instead.
+ * Arguments, layouts, alignment and errors as fds_restore_image.  One CTA per SM; a
+ * tensor-core wait that gives up (bounded) adds 1 to counter 2 of fds_counters, leaves that
+ * tile's pixels unwritten and sends the CTA's later tiles to the float32 path. */
+int fds_restore_image_tc(int32_t form, const int16_t* public_in, const uint8_t* private_in,
+                         int32_t width, int32_t height, int32_t k, const uint8_t key[16],
+                         const uint8_t iv[16], uint8_t* pixels_out, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Bit-packed storage (Sect. 6.4.3, Table 5): both fragments as bit streams instead of int16
@@ -424,8 +445,12 @@ int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]);
  * (u, v), K index 8y + x, 128-byte rows, 16-byte chunk c of row n stored at chunk c ^ (n & 7);
  * the TF32 form stores K 0..31 and K 32..63 as two consecutive 128-row blocks; the F16 form
  * has rows n = 64 l + z (z the zigzag index) of limb l of 2^13 b_u(y) b_v(x), three limbs
- * (24576 bytes).  out: host, at least 24576 (BF16, F16) or 32768 (TF32) bytes, or NULL.  *error_bound (host, or NULL): the
- * proven bound on |computed - exact| of a pre-rounding coefficient of 8-bit pixels. */
+ * (24576 bytes); FDS_TC_F16_INVERSE gives the inverse transform's table (rows n = 64 l + 8y + x
+ * of limb l of 2^9 b_u(y) b_v(x), K = the zigzag index z of (u, v), three limbs, 24576 bytes).
+ * out: host, at least 24576 (BF16, F16, F16_INVERSE) or 32768 (TF32) bytes, or NULL.
+ * *error_bound (host, or NULL): the proven bound on |computed - exact| of a pre-rounding
+ * coefficient of 8-bit pixels; for FDS_TC_F16_INVERSE, of a restored pixel value per unit of
+ * sum |q| over its channel-block's coefficients. */
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound);
 
 /* Diagnostics: the pre-rounding coefficients of the tensor-core form, laid out as in

@@ -19,6 +19,7 @@ FDS_NOALLOC_MAX_IMAGES = 4096
 FDS_TC_BF16 = 0
 FDS_TC_TF32 = 1
 FDS_TC_F16 = 2
+FDS_TC_F16_INVERSE = 3
 FDS_PACK_11 = 11
 FDS_PACK_8 = 8
 
@@ -89,6 +90,9 @@ SIGNATURES = {
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                                             ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
+    "fds_restore_image_tc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p, ctypes.c_char_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
     "fds_sizes_packed": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint64)]),

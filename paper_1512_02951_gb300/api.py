@@ -127,6 +127,22 @@ def restore_image(public: torch.Tensor, private: torch.Tensor, width: int, heigh
     return pixels_out
 
 
+def restore_image_tc(public: torch.Tensor, private: torch.Tensor, width: int, height: int, k: int,
+                     key: bytes, iv: bytes, pixels_out: torch.Tensor | None = None,
+                     form: str = "f16") -> torch.Tensor:
+    """fds_restore_image_tc: restore with the inverse transform on tensor cores (form "f16");
+    the same H x W x 3 uint8 image as restore_image, bit for bit."""
+    f = _tc_form(form)
+    dev = private.device
+    if pixels_out is None:
+        pixels_out = torch.empty((height, width, 3), dtype=torch.uint8, device=dev)
+    rc = _lib.load().fds_restore_image_tc(
+        f, public.data_ptr() if public.numel() else None, private.data_ptr(), width, height, k,
+        _check_key(key, "key"), _check_key(iv, "iv"), pixels_out.data_ptr(), _stream_ptr(dev))
+    _lib.check(rc, "fds_restore_image_tc")
+    return pixels_out
+
+
 @dataclass
 class ImageDesc:
     """One image of a batch (struct fds_image): byte offsets into the batch buffers."""
@@ -447,9 +463,11 @@ def encrypt_full(data: torch.Tensor, key: bytes, iv: bytes,
 
 def tc_basis(form: str = "bf16") -> tuple[bytes, float]:
     """fds_tc_basis (host only): the tensor-core B operand bytes and the proven bound on the
-    pre-rounding coefficient error."""
-    f = _tc_form(form)
-    n = {_lib.FDS_TC_BF16: 24576, _lib.FDS_TC_TF32: 32768, _lib.FDS_TC_F16: 24576}[f]
+    pre-rounding coefficient error ("f16_inverse": the inverse transform's table and its bound
+    per unit of sum |q|)."""
+    f = _lib.FDS_TC_F16_INVERSE if form == "f16_inverse" else _tc_form(form)
+    n = {_lib.FDS_TC_BF16: 24576, _lib.FDS_TC_TF32: 32768, _lib.FDS_TC_F16: 24576,
+         _lib.FDS_TC_F16_INVERSE: 24576}[f]
     buf = (ctypes.c_uint8 * n)()
     bound = ctypes.c_double()
     _lib.check(_lib.load().fds_tc_basis(f, buf, n, ctypes.byref(bound)), "fds_tc_basis")

@@ -40,6 +40,9 @@ __device__ __align__(16) uint4 g_tcb1[kTcBBytesTf32 / 16];
 //  g_mma_fwd  B operand of the warp-specialised tensor-core protect (f16, three limbs, rows in
 //             zigzag order), in shared-memory byte order
 __device__ __align__(16) uint4 g_mma_fwd[kMmaFwdBytes / 16];
+//  g_mma_inv  B operand of the tensor-core inverse transform (restore; f16, three limbs, K in
+//             zigzag order), in shared-memory byte order
+__device__ __align__(16) uint4 g_mma_inv[kMmaInvBytes / 16];
 
 // The exact rounding step alone: out[i] = round half away from zero of V_i, 8 V_i =
 // coords[8i] + sum_j coords[8i + j] cos(j pi/16); escalations and failures are counted like
@@ -86,6 +89,7 @@ struct DevTables {
   const uint4* tc_b[2];
   const uint4* mma_fwd;
   float mma_fwd_guard, mma_fwd_guard_rem;
+  const uint4* mma_inv;
   int sms;
 };
 DevTables g_tables[kMaxDevices];
@@ -271,6 +275,56 @@ bool build_mma_fwd(std::vector<uint8_t>& img, double* bound, double* bound_rem, 
   return true;
 }
 
+// B operand of the tensor-core inverse transform: row n = 64 l + 8 y + x holds, at K index z
+// (the zigzag index), limb l of s = 2^9 b_u(y) b_v(x), (u, v) the position of z, split as
+// s ~ L0 + L1 2^-8 + L2 2^-16 with integer limbs |L| <= 128; f16, laid out as the kernel's
+// 128-byte swizzled K-major shared-memory image.  Returns false (with a message) unless the
+// kernel's exactness argument holds: limbs exact in f16 and at most 128 in magnitude (so that
+// for coefficients |q| < 2048 every product and partial sum is an integer below 2^24), the
+// rational coefficients carried by limb 0 alone, and the per-coefficient bound the kernel's
+// guard uses, (split remainder + combining roundings) per unit of sum |q|, below 2^-24.
+// *bound gets that bound.
+bool build_mma_inv(std::vector<uint8_t>& img, double* bound, std::string& why) {
+  img.assign(kMmaInvBytes, 0);
+  double b[8][8];
+  for (int u = 0; u < 8; ++u)
+    for (int y = 0; y < 8; ++y) b[u][y] = (u == 0 ? std::sqrt(0.5) : 1.0) * 0.5 * std::cos((2 * y + 1) * u * std::acos(-1.0) / 16);
+  int uz[64], vz[64];
+  for (int u = 0; u < 8; ++u)
+    for (int v = 0; v < 8; ++v) uz[zigzag_of(u, v)] = u, vz[zigzag_of(u, v)] = v;
+  double rem_max = 0;
+  for (int p = 0; p < 64; ++p) {
+    const int y = p >> 3, x = p & 7;
+    for (int z = 0; z < 64; ++z) {
+      const int u = uz[z], v = vz[z];
+      const bool rational = (u == 0 || u == 4) && (v == 0 || v == 4);
+      double r = std::ldexp(b[u][y] * b[v][x], 9);
+      double L[3];
+      for (int l = 0; l < 3; ++l) {
+        if (l) r = std::ldexp(r, 8);
+        L[l] = std::nearbyint(r);
+        r -= L[l];
+        if (std::fabs(L[l]) > 128.0) return (why = "inverse limb above 128"), false;
+      }
+      if (rational && (std::fabs(L[0]) != 64.0 || L[1] != 0.0 || L[2] != 0.0))
+        return (why = "rational coefficient not carried by limb 0 alone"), false;
+      rem_max = std::max(rem_max, std::ldexp(std::fabs(r), -25));   // |basis - limbs|
+      for (int l = 0; l < 3; ++l) {
+        const int n = 64 * l + p;
+        const uint16_t h = f16_of_int((int)L[l]);
+        std::memcpy(&img[n * 128 + (((z >> 3) ^ (n & 7)) << 4) + (z & 7) * 2], &h, 2);
+      }
+    }
+  }
+  // per unit of sum |q|: the split remainder, and the two fused multiply-adds that combine the
+  // limb accumulators (each accumulator at most 128 sum |q|; half an ulp relative, 2^-24, of
+  // t1 = D1 + D2 2^-8 and of t2 = D0 + t1 2^-8, then scaled by 2^-9), plus cos() in double
+  const double comb = std::ldexp(128.0 * (1.0 + 2.0 / 256.0 + 1.0 / 65536.0), -24 - 9);
+  *bound = rem_max + comb + std::ldexp(1.0, -45);
+  if (*bound >= std::ldexp(1.0, -24)) return (why = "inverse limb split too coarse"), false;
+  return true;
+}
+
 // Initialise the current device (once) and return its index in *dev_out.
 int ensure_init(int* dev_out = nullptr) {
   int dev = 0;
@@ -375,6 +429,17 @@ int ensure_init(int* dev_out = nullptr) {
     // the guard the kernel compares with, rounded up: float(bound) * (1 + 2^-20)
     tb.mma_fwd_guard = (float)(mf_bound * (1.0 + std::ldexp(1.0, -20)));
     tb.mma_fwd_guard_rem = (float)(mf_rem * (1.0 + std::ldexp(1.0, -20)));
+  }
+  {
+    static std::vector<uint8_t> mi;
+    static double mi_bound = 0;
+    static bool mi_ok = false;
+    static std::string mi_why;
+    if (mi.empty()) mi_ok = build_mma_inv(mi, &mi_bound, mi_why);
+    if (!mi_ok) return set_err(FDS_E_INVALID, "tensor-core inverse table: " + mi_why);
+    if ((e = cudaMemcpyToSymbol(g_mma_inv, mi.data(), mi.size())) != cudaSuccess) return cuda_fail(e, "table upload");
+    if ((e = cudaGetSymbolAddress(&p, g_mma_inv)) != cudaSuccess) return cuda_fail(e, "symbol address");
+    tb.mma_inv = static_cast<const uint4*>(p);
   }
   if ((e = upload_sha512_constants()) != cudaSuccess) return cuda_fail(e, "SHA-512 constants upload");
   if ((e = upload_dwt_constants()) != cudaSuccess) return cuda_fail(e, "SHA constants upload");
@@ -641,6 +706,32 @@ int fds_protect_image_tc(int32_t form, const uint8_t* pixels, int32_t width, int
     e = launch_protect_tc(a, (cudaStream_t)stream, form, false, g_tables[dev].sms);
   }
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core protect launch");
+}
+
+int fds_restore_image_tc(int32_t form, const int16_t* public_in, const uint8_t* private_in, int32_t width,
+                         int32_t height, int32_t k, const uint8_t key[16], const uint8_t iv[16],
+                         uint8_t* pixels_out, void* stream) {
+  if (form != FDS_TC_F16) return set_err(FDS_E_INVALID, "the tensor-core inverse takes form FDS_TC_F16");
+  if (bad_dims(width, height)) return set_err(FDS_E_INVALID, "width and height must be positive multiples of 8");
+  if (k < 0 || k > 63) return set_err(FDS_E_INVALID, "k must be in 0..63");
+  if (!pixels_out || !key || !iv || !private_in || (k < 63 && !public_in))
+    return set_err(FDS_E_INVALID, "null pointer argument");
+  if (misaligned(pixels_out, 8) || misaligned(public_in, 16) || misaligned(private_in, 16))
+    return set_err(FDS_E_INVALID, "pixels must be 8-byte aligned, fragments 16-byte aligned");
+  int dev = 0;
+  int rc = ensure_init(&dev);
+  if (rc) return rc;
+  TileArgs a{};
+  a.pub_in = public_in;
+  a.priv_in = private_in;
+  a.pixels_out = pixels_out;
+  fill_geometry(a, width, height, k);
+  expand_key(key, a.rk);
+  iv_words(iv, &a.iv_hi, &a.iv_lo);
+  set_tables(a, dev);
+  a.tc_b = g_tables[dev].mma_inv;
+  const cudaError_t e = launch_restore_tc(a, (cudaStream_t)stream, g_tables[dev].sms);
+  return e == cudaSuccess ? FDS_OK : cuda_fail(e, "tensor-core restore launch");
 }
 
 int fds_encrypt_full(const uint8_t* in, uint8_t* out, uint64_t bytes, const uint8_t key[16], const uint8_t iv[16],
@@ -1127,13 +1218,15 @@ int fds_sha512_constants(uint64_t k_out[80], uint64_t h0_out[8]) {
 }
 
 int fds_tc_basis(int32_t form, uint8_t* out, uint64_t bytes, double* error_bound) {
-  if (form != FDS_TC_BF16 && form != FDS_TC_TF32 && form != FDS_TC_F16)
+  if (form != FDS_TC_BF16 && form != FDS_TC_TF32 && form != FDS_TC_F16 && form != FDS_TC_F16_INVERSE)
     return set_err(FDS_E_INVALID, "unknown tensor-core form");
   std::vector<uint8_t> img;
   std::string why;
   double bound = 0;
   double rem = 0;
-  const bool ok = form == FDS_TC_F16 ? build_mma_fwd(img, &bound, &rem, why) : build_tc_b(form, img, why, &bound);
+  const bool ok = form == FDS_TC_F16_INVERSE ? build_mma_inv(img, &bound, why)
+                  : form == FDS_TC_F16       ? build_mma_fwd(img, &bound, &rem, why)
+                                             : build_tc_b(form, img, why, &bound);
   if (error_bound) *error_bound = bound;
   if (!ok) return set_err(FDS_E_INVALID, "tensor-core table: " + why);
   if (out) {

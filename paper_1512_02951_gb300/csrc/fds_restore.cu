@@ -26,7 +26,7 @@
 // the same kernel with the private positions "padded with zeros" -- the private staging
 // holds the constant (1024, 0, .., 0) per channel-block (DC 8 x 128: the zero-mean block
 // shifted to mid-grey), nothing private is loaded or decrypted.
-#include "fds_tile.cuh"
+#include "fds_mma.cuh"
 
 namespace fds {
 
@@ -49,6 +49,19 @@ constexpr int kSmemBytesPacked = kSmemLand + kLandBytes;
 // tiles mostly carry little keystream, was slower with it, 2.96 -> 3.11 ms on 2000 images)
 constexpr int kSmemTrep = kSmemBytes;
 constexpr int kSmemBytesRep = kSmemTrep + 4 * kTrepWords;
+// tensor-core inverse (TC): after the rest, on a 1024-byte boundary, the A operand (256 rows
+// of 64 f16 coefficients: the tile's 192 channel-blocks as two MMA row blocks of 128) and the
+// B operand (the inverse basis, three f16 limbs x 64 pixels), an mbarrier and the TMEM address
+constexpr int kTcA = 256 * 128;
+constexpr int kSmemBytesTc = kSmemBytesRep + 1024 + kTcA + kMmaInvBytes + 16;
+constexpr int kTcCols = 2 * 192;                       // accumulator columns: 2 row blocks x 3 limbs x 64
+static_assert(kTcCols <= 512, "TMEM columns");
+constexpr uint32_t kTcInvIdesc = idesc_f16(192, false);
+// guard of the TC inverse, per channel-block with S = sum |q|: S 2^-24 + 2^-22 (the host
+// proves, when it builds the limb table, that split remainder plus combining roundings stay
+// below S 2^-24, and refuses otherwise; 2^-22 covers the roundings of the guard itself)
+constexpr float kTcInvGuardS = 1.0f / 16777216.0f;
+constexpr float kTcInvGuard0 = 1.0f / 4194304.0f;
 
 // ---- packed storage: land, decrypt, unpack one tile
 template <int W>
@@ -257,8 +270,12 @@ __device__ __forceinline__ void decrypt_fragments(const TileSlot* sl, const uint
 
 // BATCH: tiles of many images (round keys from the slot); else one image (round keys read
 // from the kernel parameters, which AES then takes as constant-bank operands)
-template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0>
-__global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
+// TC: the inverse transform as tcgen05 MMAs (one image, int16 storage; a.tc_b = the inverse
+// basis table); a tile holding a coefficient of magnitude 2048 or more takes the float32
+// butterflies instead.
+template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0, bool TC = false>
+__global__ void __launch_bounds__(kThreads, TC ? 1 : kRCtasPerSm) restore_kernel(const __grid_constant__ TileArgs a) {
+  static_assert(!TC || (!BATCH && !PUBIMG && PACK == 0), "tensor-core inverse: one image, int16 storage");
   extern __shared__ __align__(128) uint8_t smem[];
   // AES tables: T0 replicated per lane (one image, int16 storage, private fragment decrypted),
   // else the four T-tables
@@ -281,6 +298,7 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
   }
   if (t < 4) misc[t] = 0;
   if (t == 0) {
+    misc[6] = 0;                         // TC: a tensor-core wait gave up
     misc[4] = next_tile(a, 0, blockIdx.x, gridDim.x);
     misc[5] = next_tile(a, 1, blockIdx.x, gridDim.x);
   }
@@ -289,9 +307,25 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   uint32_t phase[2] = {0u, 0u};
   int lost = 0;
+  // TC: operands, MMA barrier, TMEM (kTcCols columns rounded up to 512)
+  uint8_t* const tcbase = TC ? reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem + kSmemBytesRep) + 1023) &
+                                                          ~(uintptr_t)1023)
+                             : nullptr;
+  uint8_t* const tA = tcbase;
+  uint8_t* const tB = TC ? tcbase + kTcA : nullptr;
+  uint64_t* const tbar = TC ? reinterpret_cast<uint64_t*>(tcbase + kTcA + kMmaInvBytes) : nullptr;
+  uint32_t* const tslot = TC ? reinterpret_cast<uint32_t*>(tcbase + kTcA + kMmaInvBytes + 8) : nullptr;
+  if constexpr (TC) {
+    for (int i = t; i < kMmaInvBytes / 16; i += kThreads) reinterpret_cast<uint4*>(tB)[i] = a.tc_b[i];
+    for (int i = t; i < 64 * 128 / 16; i += kThreads)    // A rows 192..255 (never a channel-block)
+      reinterpret_cast<uint4*>(tA + 192 * 128)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (t < 32) tmem_alloc<512>(tslot);
+    fence_proxy_async();
+  }
   if (t == 0) {
     mbar_init(bars);
     mbar_init(bars + 1);
+    if constexpr (TC) mbar_init(tbar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if constexpr (PUBIMG) {   // the private staging of both areas: (1024, 0, .., 0) per channel-block
@@ -323,6 +357,13 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
   // a fragment load that did not complete in time leaves its tile's pixels unwritten (the
   // failure counter records it): cur_lost for the tile being transformed, lost counts them all
   int cur_lost = lost;
+  uint32_t tmem = 0, tphase = 0;
+  if constexpr (TC) {
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    tmem = *tslot;
+  }
   for (int it = 0;; ++it) {
     const int buf = it & 1;
     const int cur = misc[4 + buf], nxt = misc[4 + (buf ^ 1)];
@@ -349,7 +390,106 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
     const int16_t* pubst = reinterpret_cast<const int16_t*>(stage(buf));
     const int16_t* privst = reinterpret_cast<const int16_t*>(stage(buf) + kTileCb * 2 * npub);
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
-    if (b < nb) {
+    uint8_t* out = pix + b * 24 + c;
+    uint32_t mlo = 0, mhi = 0;
+    // one row of restored values: clamp, round, mark the values within the guard of a
+    // half-integer, bytes into the interleaved pixel tile
+    auto emit_row = [&](int y, const float (&row)[8], float thr) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 pc = make_float2(fminf(fmaxf(row[2 * j], 0.0f), 255.0f), fminf(fmaxf(row[2 * j + 1], 0.0f), 255.0f));
+        const float2 yv = add2(pc, make_float2(kMagic, kMagic));
+        const float2 r = sub2(pc, add2(yv, make_float2(-kMagic, -kMagic)));
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const int x = 2 * j + l;
+          if (fabsf(l ? r.y : r.x) > thr) {
+            if (8 * y + x < 32)
+              mlo |= 1u << (8 * y + x);
+            else
+              mhi |= 1u << (8 * y + x - 32);
+          }
+          out[y * kRowBytes + 3 * x] = (uint8_t)__float_as_uint(l ? yv.y : yv.x);
+        }
+      }
+    };
+    bool tc_done = false;
+    if constexpr (TC) {
+      // A row t: the channel-block's 64 coefficients in zigzag order (the K order of the
+      // basis table), as f16 -- exact for |q| < 2048; S = sum |q| sizes the guard
+      int S = 0;
+      bool big = false;
+      if (b < nb) {
+        const int16_t* pub_cb = pubst + cb * npub;
+        const int16_t* priv_cb = privst + cb * (k + 1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          uint32_t w[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int z0 = 8 * j + 2 * m, z1 = z0 + 1;
+            const int q0 = z0 <= k ? priv_cb[z0] : pub_cb[z0 - k - 1];
+            const int q1 = z1 <= k ? priv_cb[z1] : pub_cb[z1 - k - 1];
+            const int m0 = q0 < 0 ? -q0 : q0, m1 = q1 < 0 ? -q1 : q1;
+            S += m0 + m1;
+            big |= (m0 | m1) >= 2048;
+            const __half2 h = __floats2half2_rn((float)q0, (float)q1);
+            w[m] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          *reinterpret_cast<uint4*>(tA + sw128_offset(t, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      fence_proxy_async();
+      if (!__syncthreads_or(big || misc[6] != 0)) {                           // A2
+        if (t == 0) {
+          tc_fence_after_sync();
+          const uint32_t a0 = smem_u32(tA), b0 = smem_u32(tB);
+#pragma unroll
+          for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_f16(tmem + 192u * rb, sw128_kmajor_desc(a0 + rb * 128 * 128) + 2 * ks, sw128_kmajor_desc(b0) + 2 * ks,
+                      kTcInvIdesc, ks > 0 ? 1u : 0u);
+          mma_commit(tbar);
+        }
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(tbar, tphase));
+        tphase ^= 1u;
+        tc_fence_after_sync();
+        if (!ok) {                               // the tile's pixels stay unwritten; later
+          ++cur_lost;                            // tiles take the float32 path
+          ++lost;
+          if ((t & 31) == 0) misc[6] = 1;
+        }
+        // this warp's TMEM lanes: row block t / 128, lanes 32 (warp % 4) ..
+        const int warp = t >> 5;
+        const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (warp >= 4 ? 192u : 0u);
+        const float thr = 0.5f - fmaf((float)S, kTcInvGuardS, kTcInvGuard0);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {          // pixel rows 2h and 2h + 1
+          uint32_t d0[16], d1[16], d2[16];
+          tmem_ld16(tl + 16 * h, d0);
+          tmem_ld16(tl + 64 + 16 * h, d1);
+          tmem_ld16(tl + 128 + 16 * h, d2);
+          tmem_ld_wait();
+          if (ok && b < nb) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+              float row[8];
+#pragma unroll
+              for (int x = 0; x < 8; ++x) {
+                const int i = 8 * rr + x;
+                row[x] = fmaf(fmaf(__uint_as_float(d2[i]), 1.0f / 256.0f, __uint_as_float(d1[i])), 1.0f / 256.0f,
+                              __uint_as_float(d0[i])) * (1.0f / 512.0f);
+              }
+              emit_row(2 * h + rr, row, thr);
+            }
+          }
+        }
+        tc_fence_before_sync();
+        tc_done = true;
+      }
+    }
+    if (!tc_done && b < nb) {
       const int16_t* pub_cb = pubst + cb * npub;
       const int16_t* priv_cb = privst + cb * (k + 1);
       // coefficients as pairs of adjacent columns: the column pass runs on two columns per
@@ -378,8 +518,6 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
         for (int y = 0; y < 8; ++y) G[y][j] = col[y];
       }
       const float thr = 0.5f - l1 * kGuardInvScale;
-      uint8_t* out = pix + b * 24 + c;
-      uint32_t mlo = 0, mhi = 0;
 #pragma unroll
       for (int y = 0; y < 8; ++y) {
         float row[8];
@@ -389,24 +527,10 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
           row[2 * j + 1] = G[y][j].y;
         }
         idct8(row);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float2 pc = make_float2(fminf(fmaxf(row[2 * j], 0.0f), 255.0f), fminf(fmaxf(row[2 * j + 1], 0.0f), 255.0f));
-          const float2 yv = add2(pc, make_float2(kMagic, kMagic));
-          const float2 r = sub2(pc, add2(yv, make_float2(-kMagic, -kMagic)));
-#pragma unroll
-          for (int l = 0; l < 2; ++l) {
-            const int x = 2 * j + l;
-            if (fabsf(l ? r.y : r.x) > thr) {
-              if (8 * y + x < 32)
-                mlo |= 1u << (8 * y + x);
-              else
-                mhi |= 1u << (8 * y + x - 32);
-            }
-            out[y * kRowBytes + 3 * x] = (uint8_t)__float_as_uint(l ? yv.y : yv.x);
-          }
-        }
+        emit_row(y, row, thr);
       }
+    }
+    if (b < nb) {
       uint64_t mask = ((uint64_t)mhi << 32) | mlo;
       while (mask) {
         const int pos = __ffsll((long long)mask) - 1;
@@ -489,7 +613,12 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
   }
   if (esc) atomicAdd(&misc[2], esc);
   if (fail || lost) atomicAdd(&misc[3], 1);
+  if constexpr (TC) tc_fence_before_sync();
   __syncthreads();
+  if constexpr (TC) {
+    tc_fence_after_sync();
+    if (t < 32) tmem_dealloc<512>(tmem);
+  }
   if (t == 0) bulk_wait_all();
   if (t == 0 && a.counters) {
     if (misc[1]) atomicAdd(&a.counters[0], (unsigned long long)misc[1]);
@@ -498,19 +627,28 @@ __global__ void __launch_bounds__(kThreads, kRCtasPerSm) restore_kernel(const __
   }
 }
 
-template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0>
+template <int K, bool BATCH, bool PUBIMG = false, int PACK = 0, bool TC = false>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
   static int resident[kMaxAttrDevices];
-  constexpr int smem = PACK ? kSmemBytesPacked : (BATCH || PUBIMG ? kSmemBytes : kSmemBytesRep);
-  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG, PACK>, smem, attr);
+  constexpr int smem = TC ? kSmemBytesTc : (PACK ? kSmemBytesPacked : (BATCH || PUBIMG ? kSmemBytes : kSmemBytesRep));
+  cudaError_t e = smem_attr_once(restore_kernel<K, BATCH, PUBIMG, PACK, TC>, smem, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
-  const int r = resident_ctas(restore_kernel<K, BATCH, PUBIMG, PACK>, kThreads, smem, resident);
+  const int r = resident_ctas(restore_kernel<K, BATCH, PUBIMG, PACK, TC>, kThreads, smem, resident);
   const int cap = (per_sm >= 1 && per_sm < r ? per_sm : r) * sms;
   const int grid = ntiles < cap ? ntiles : cap;
-  if (grid > 0) restore_kernel<K, BATCH, PUBIMG, PACK><<<grid, kThreads, smem, s>>>(a);
+  if (grid > 0) restore_kernel<K, BATCH, PUBIMG, PACK, TC><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// the tensor-core inverse form (one image, int16 storage; a.tc_b = the inverse basis table),
+// one CTA per SM (the operands and TMEM take what a second CTA would need)
+cudaError_t launch_restore_tc(const TileArgs& a, cudaStream_t s, int sms) {
+  if (a.images || a.k < 0 || a.public_image || a.pack || a.plain_private || !a.tc_b) return cudaErrorInvalidValue;
+  if (a.k == 0) return launch_k<0, false, false, 0, true>(a, s, sms, 1);
+  if (a.k == 5) return launch_k<5, false, false, 0, true>(a, s, sms, 1);
+  return launch_k<-1, false, false, 0, true>(a, s, sms, 1);
 }
 
 // k is uniform over the launch when a.k >= 0; a.k < 0 (batches of mixed k) reads k per tile;

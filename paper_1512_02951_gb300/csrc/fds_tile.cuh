@@ -36,6 +36,9 @@ constexpr int kTcBBytesTf32 = 2 * 128 * 128;  // 2 limbs x 64 rows x 64 tf32, as
 #endif
 constexpr int kMmaFwdLimbs = FDS_MMA_LIMBS;
 constexpr int kMmaFwdBytes = kMmaFwdLimbs * 64 * 128;
+// tensor-core inverse transform (restore): three f16 limbs x 64 pixel rows x 64 f16 (K in
+// zigzag order); coefficients |q| < 2048 go in exactly as f16
+constexpr int kMmaInvBytes = 3 * 64 * 128;
 
 // Forward guard.  On level-shifted pixels |p - 128| <= 128 the butterflies are within
 // 1.11e-3 of the exact coefficient (first-order bound: every rounded operation and every
@@ -129,6 +132,8 @@ constexpr int32_t kPxIn16 = 1, kPxOut16 = 2;
 // residency
 cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 0);
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 0);
+// restore with the inverse transform on tensor cores (one image, int16 storage)
+cudaError_t launch_restore_tc(const TileArgs& a, cudaStream_t s, int sms);
 // tensor-core protect of one image (form 0: BF16 three limbs, 1: TF32 two limbs); tiles of
 // 128 channel-blocks, two CTAs per SM
 cudaError_t launch_protect_tc(const TileArgs& a, cudaStream_t s, int form, bool debug, int sms);

@@ -1,8 +1,8 @@
 """Whole-output parity at the benchmark sizes, through the C ABI, against the CPU oracle.
 
   * the 4096 x 4096 RGB image (the benchmark workload) at k = 0 and k = 5: every public int16,
-    every ciphertext byte and every restored pixel, for the float32 CUDA-core kernels and for
-    the three tensor-core forms of protect;
+    every ciphertext byte and every restored pixel, for the float32 CUDA-core kernels, the
+    three tensor-core forms of protect and the tensor-core inverse of restore;
   * the per-block float32 error guard of the protect kernel, u (2.7 V + 0.9 W + 1), on every
     channel-block of that image and of a 200-image batch of uneven sizes;
   * the batched plan (one persistent launch per direction over a 2000-image batch of uneven
@@ -78,6 +78,17 @@ def test_4096_whole_image_tensor_core_forms_bit_exact(api, form, k):
     pub_h = pub.cpu().numpy()
     assert np.array_equal(pub_h, want_pub), _first_diff(pub_h, want_pub)
     assert priv.cpu().numpy().tobytes() == want_priv, f"{form}: private ciphertext differs"
+
+
+@pytest.mark.parametrize("k", [0, 5])
+def test_4096_whole_image_tensor_core_restore_bit_exact(api, k):
+    img, key, iv, want_pub, want_priv, want_back = _oracle(k)
+    pub = torch.from_numpy(want_pub).to(DEV)
+    priv = torch.from_numpy(np.frombuffer(want_priv, dtype=np.uint8).copy()).to(DEV)
+    back = api.restore_image_tc(pub, priv, W, H, k, key, iv)
+    torch.cuda.synchronize()
+    back_h = back.cpu().numpy()
+    assert np.array_equal(back_h, want_back), _first_diff(back_h, want_back)
 
 
 def _pass_weight(x):

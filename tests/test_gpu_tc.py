@@ -126,3 +126,67 @@ def test_tc_queue_overflow(api, form):
     api.counters(reset=True)
     _check(api, img, 5, form, seed=12)
     assert api.counters()[0] > 8 * 64 * 3 * best_n // 2
+
+
+# ---- the inverse transform on tensor cores (restore, form f16) ----------------------------
+
+def _tc_restore(api, pub, priv, w, h, k, key, iv):
+    pub_d = torch.from_numpy(np.ascontiguousarray(pub)).to(DEV)
+    priv_d = torch.from_numpy(np.frombuffer(priv, dtype=np.uint8).copy()).to(DEV)
+    out = api.restore_image_tc(pub_d, priv_d, w, h, k, key, iv)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("w,h", [(8, 8), (16, 8), (64, 64), (136, 72), (520, 40), (512, 512)])
+@pytest.mark.parametrize("k", [0, 5, 17, 63])
+def test_tc_restore_of_protected_images(api, w, h, k):
+    img = synth.make_image(w, h, 70 + w + h)
+    key, iv = synth.make_key(71), synth.make_iv(72)
+    pub, priv = ofds.protect(img, key, iv, k)
+    got = _tc_restore(api, pub, priv, w, h, k, key, iv)
+    want = ofds.restore(pub, priv, key, iv, k, w, h)
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, f"{len(bad)} pixel mismatches, first {bad[:5].tolist()}"
+
+
+def test_tc_restore_of_arbitrary_int16_fragments(api):
+    # any int16 input: tiles holding |q| >= 2048 take the float32 butterflies, the others the
+    # MMA; both must give the oracle's bytes, and so must blocks whose pixels are exact ties
+    from oracle import aes as oaes
+    rng = np.random.default_rng(19)
+    w, h, k = 520, 48, 5                  # 390 blocks: seven tiles, the last one partial
+    by, bx = h // 8, w // 8
+    pub = rng.integers(-60, 60, (by, bx, 3, 63 - k)).astype(np.int16)
+    plain = rng.integers(-300, 2040, (by, bx, 3, k + 1)).astype("<i2")
+    pub[0, 0, 0, :] = rng.integers(-32768, 32767, 63 - k)      # tile 0: fallback
+    pub[3, 40, 1, :3] = 32767                                    # a later tile: fallback
+    plain[5, 60, 2, 0] = -32768
+    pub[2, 3, :, :] = 0                                          # only DC, DC = 4 mod 8: ties
+    plain[2, 3, :, 1:] = 0
+    plain[2, 3, :, 0] = [1004, 1020, 12]
+    pub[1, 20, :, :] = rng.integers(-2047, 2048, (3, 63 - k))   # large but below 2048: MMA
+    key, iv = synth.make_key(25), synth.make_iv(26)
+    priv = oaes.ctr_xcrypt(key, iv, plain.tobytes())
+    got = _tc_restore(api, pub, priv, w, h, k, key, iv)
+    want = ofds.restore(pub, priv, key, iv, k, w, h)
+    assert np.array_equal(got, want)
+    # and the float32 CUDA-core restore gives the same bytes
+    pub_d = torch.from_numpy(pub).to(DEV)
+    priv_d = torch.from_numpy(np.frombuffer(priv, dtype=np.uint8).copy()).to(DEV)
+    ref = api.restore_image(pub_d, priv_d, w, h, k, key, iv)
+    torch.cuda.synchronize()
+    assert np.array_equal(ref.cpu().numpy(), got)
+
+
+def test_tc_restore_4096_equals_float32_path(api):
+    w = h = 4096
+    img = synth.make_image(w, h, 2)
+    key, iv = synth.make_key(81), synth.make_iv(82)
+    x = torch.from_numpy(img).to(DEV)
+    pub, priv = api.protect_image(x, key, iv, 5)
+    a = api.restore_image(pub, priv, w, h, 5, key, iv)
+    b = api.restore_image_tc(pub, priv, w, h, 5, key, iv)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert 0.88 < (b == x).double().mean().item() < 0.97

@@ -114,3 +114,50 @@ def test_tc_host_argument_checks(api):
     assert lib.fds_tc_basis(0, small, 16, None) == -1
     with pytest.raises(ValueError):
         api.tc_basis("fp8")
+
+
+def _decode_inverse(img):
+    """limbs[l, p, z] of the inverse table: row n = 64 l + p (p = 8y + x), K index z (zigzag)."""
+    raw = np.frombuffer(img, dtype=np.uint8)
+    limbs = np.zeros((3, 64, 64))
+    for l in range(3):
+        for p in range(64):
+            n = 64 * l + p
+            for z in range(64):
+                off = n * 128 + (((z >> 3) ^ (n & 7)) << 4) + (z & 7) * 2
+                limbs[l, p, z] = float(raw[off:off + 2].view(np.float16)[0])
+    return limbs
+
+
+def test_inverse_limbs_reconstruct_the_transposed_basis(api):
+    img, bound = api.tc_basis("f16_inverse")
+    limbs = _decode_inverse(img)
+    assert np.all(limbs == np.round(limbs)) and np.abs(limbs).max() <= 128
+    b = odct.basis_matrix()
+    basis = np.einsum("uy,vx->uvyx", b, b).reshape(64, 64)      # [8u+v, 8y+x]
+    zz = _zigzag()
+    inv = basis[zz, :].T                                         # [8y+x, zigzag z]
+    approx = limbs[0] * 2.0 ** -9 + limbs[1] * 2.0 ** -17 + limbs[2] * 2.0 ** -25
+    rem = np.abs(inv - approx)
+    assert rem.max() <= 2.0 ** -26 * (1 + 1e-9)                 # half a unit of the last limb
+    # the bound per unit of sum |q| covers the remainder and stays below the kernel's 2^-24
+    assert rem.max() <= bound < 2.0 ** -24
+    # coefficients below 2048 keep every partial sum of every limb an integer below 2^24
+    assert (2047 * np.abs(limbs).sum(axis=2)).max() < 2 ** 24
+    # the rational basis functions ((u, v) in {0, 4}^2: +-1/8) sit in limb 0 alone
+    for u in (0, 4):
+        for v in (0, 4):
+            z = zz.index(8 * u + v)
+            assert np.all(np.abs(limbs[0, :, z]) == 64) and not limbs[1:, :, z].any()
+
+
+def test_tc_restore_host_argument_checks(api):
+    from paper_1512_02951_gb300 import _lib
+    lib = _lib.load()
+    key = bytes(16)
+    assert lib.fds_restore_image_tc(0, 16, 16, 64, 64, 5, key, key, 8, None) == -1   # not the f16 form
+    assert b"FDS_TC_F16" in lib.fds_last_error()
+    assert lib.fds_restore_image_tc(2, 16, 16, 100, 64, 5, key, key, 8, None) == -1  # width
+    assert lib.fds_restore_image_tc(2, 16, 16, 64, 64, 64, key, key, 8, None) == -1  # k
+    assert lib.fds_restore_image_tc(2, 24, 16, 64, 64, 5, key, key, 8, None) == -1   # alignment
+    assert lib.fds_restore_image_tc(2, 16, None, 64, 64, 5, key, key, 8, None) == -1  # null
