@@ -749,7 +749,7 @@ int fds_encrypt_full(const uint8_t* in, uint8_t* out, uint64_t bytes, const uint
   uint64_t hi, lo;
   iv_words(iv, &hi, &lo);
   const cudaError_t e = launch_aes_full(in, out, bytes, hi, lo, rk, g_tables[dev].T, (cudaStream_t)stream,
-                                        g_tables[dev].sms);
+                                        g_tables[dev].sms, g_tables[dev].counters);
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "full encryption launch");
 }
 
@@ -833,7 +833,7 @@ int fds_restore_image_packed(int32_t form, const uint8_t* public_in, const uint8
   uint64_t hi, lo;
   iv_words(iv, &hi, &lo);
   cudaError_t e = launch_aes_full(private_in, s_plain, vpk, hi, lo, rk, g_tables[dev].T, s,
-                                  g_tables[dev].sms);   // 1. decrypt the packed private stream
+                                  g_tables[dev].sms, g_tables[dev].counters);   // 1. decrypt the packed private stream
   if (e != cudaSuccess) return cuda_fail(e, "decryption launch");
   const long long ncb = 3ll * (width / 8) * (long long)(height / 8);
   e = launch_unpack(public_in, s_plain, s_pub, reinterpret_cast<int16_t*>(s_priv), ncb, k, form, s);
@@ -1121,7 +1121,7 @@ int fds_protect_image_strong(const uint8_t* pixels, int32_t width, int32_t heigh
   cudaError_t e = launch_strong_mask(s_plain, public_image_out, public_image_out, width, height, k, s);
   if (e != cudaSuccess) return cuda_fail(e, "mask launch");   // 3. XOR the SHA-512 masks
   e = launch_aes_full(s_plain, private_out, priv16, a.iv_hi, a.iv_lo, a.rk, g_tables[dev].T, s,
-                      g_tables[dev].sms);        // 4. encrypt Part 1
+                      g_tables[dev].sms, g_tables[dev].counters);        // 4. encrypt Part 1
   return e == cudaSuccess ? FDS_OK : cuda_fail(e, "encryption launch");
 }
 
@@ -1145,7 +1145,7 @@ int fds_restore_image_strong(const uint8_t* public_image_in, const uint8_t* priv
   uint64_t hi, lo;
   iv_words(iv, &hi, &lo);
   cudaError_t e = launch_aes_full(private_in, s_plain, priv16, hi, lo, rk, g_tables[dev].T, s,
-                                  g_tables[dev].sms);   // 1. decrypt Part 1
+                                  g_tables[dev].sms, g_tables[dev].counters);   // 1. decrypt Part 1
   if (e != cudaSuccess) return cuda_fail(e, "decryption launch");
   e = launch_strong_mask(s_plain, public_image_in, s_img, width, height, k, s);
   if (e != cudaSuccess) return cuda_fail(e, "mask launch");   // 2. remove the masks

@@ -7,9 +7,11 @@
 
 namespace fds {
 
-// AES-128-CTR over a whole buffer (the full-encryption comparator)
+// AES-128-CTR over a whole buffer (the full-encryption comparator); counters: the device's
+// three counters (the failure counter records a launch that could not place its table)
 cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,
-                            const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms);
+                            const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms,
+                            unsigned long long* counters);
 // histogram and adjacent-pair sums of an H x W x 3 image (hist [3][256], sums [3][3][6],
 // both zero on entry)
 cudaError_t launch_image_stats(const uint8_t* img, int width, int height, unsigned long long* hist, long long* sums,

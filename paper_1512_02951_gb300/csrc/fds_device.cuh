@@ -383,6 +383,76 @@ __device__ __forceinline__ void aes128_encrypt_rep_n(uint32_t (&s)[M][4], const 
   }
 }
 
+// AES-128 with the pair table: T0 and T2 = rotl(T0, 16), each replicated per lane, in one
+// 64 KB table that starts at shared-window address kTpairWin (a multiple of 64 KB).  Entry x
+// of table j (0: T0, 1: T2), copy L, is the word at window address kTpairWin + 256 x + 128 j +
+// 4 L; lane L reads copy L, so a warp's 32 lookups fall in 32 distinct banks.  One byte
+// permute forms the whole address of a lookup: the state byte goes to bits 8..15 and the
+// lane's constant supplies bits 0..7 (128 j + 4 L) and 16..31 (kTpairWin >> 16), so a lookup
+// is a permute and a load, with no address arithmetic.  The two other tables are rotations:
+// T1 = rotl(T0, 8) and T3 = rotl(T2, 8), so column c of a middle round is
+//   T0[s_c.0] ^ T2[s_{c+2}.2] ^ rk_c ^ rotl8(T0[s_{c+1}.1] ^ T2[s_{c+3}.3]),
+// one rotation per column.  In the last round S[x] is byte 1 and byte 2 of T0[x] and byte 0
+// and byte 3 of T2[x], so each output byte is taken where it already sits.  Measured alone
+// (GB300, one CTA of 1024 threads per SM): 596 instructions and 6.3 SM cycles per keystream
+// block against 800 and 8.15 with T0 replicated in a 32 KB table (the same table placed at
+// an arbitrary address costs an add per lookup: 750 and 8.0).
+constexpr uint32_t kTpairWin = 0x10000u;
+constexpr int kTpairBytes = 65536;
+
+// the lane's constants for T0 and T2 lookups.  The lane index is read from %laneid where the
+// constants are needed (a volatile read the compiler does not hoist), so that they are not
+// kept live through a kernel's other phases.
+struct PairLanes {
+  uint32_t c0, c2;
+};
+__device__ __forceinline__ PairLanes pair_lanes() {
+  uint32_t lane;
+  asm volatile("mov.u32 %0, %%laneid;" : "=r"(lane));
+  const uint32_t hi = kTpairWin & 0xffff0000u, l4 = 4u * lane;
+  return PairLanes{hi | l4, hi | (128u + l4)};
+}
+// byte X of w looked up in the table whose lane constant is lc
+template <int X>
+__device__ __forceinline__ uint32_t tpair(uint32_t w, uint32_t lc) {
+  return lds_u32(__byte_perm(w, lc, 0x7604u | ((uint32_t)X << 4)));
+}
+// Fill the pair table at `tab` (shared memory, window address kTpairWin) from T0 in global
+// memory (256 words): threads t = 0 .. nthreads - 1 of the CTA; a barrier must follow
+__device__ __forceinline__ void fill_pair_table(uint8_t* tab, const uint32_t* T0, int t, int nthreads) {
+  for (int i = t; i < 2048; i += nthreads) {
+    const int x = i >> 3, m = i & 7;
+    const uint32_t t0 = __ldg(T0 + x), t2 = __byte_perm(t0, t0, 0x1032u);
+    reinterpret_cast<uint4*>(tab + 256 * x)[m] = make_uint4(t0, t0, t0, t0);
+    reinterpret_cast<uint4*>(tab + 256 * x + 128)[m] = make_uint4(t2, t2, t2, t2);
+  }
+}
+__device__ __forceinline__ void aes128_encrypt_pair(uint32_t (&s)[4], const uint32_t* rk, PairLanes lc) {
+  auto r8 = [](uint32_t x) { return __byte_perm(x, x, 0x2103u); };
+  uint32_t s0 = s[0] ^ rk[0], s1 = s[1] ^ rk[1], s2 = s[2] ^ rk[2], s3 = s[3] ^ rk[3];
+#pragma unroll 1
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t n0 = tpair<0>(s0, lc.c0) ^ tpair<2>(s2, lc.c2) ^ rk[4 * r] ^ r8(tpair<1>(s1, lc.c0) ^ tpair<3>(s3, lc.c2));
+    const uint32_t n1 = tpair<0>(s1, lc.c0) ^ tpair<2>(s3, lc.c2) ^ rk[4 * r + 1] ^ r8(tpair<1>(s2, lc.c0) ^ tpair<3>(s0, lc.c2));
+    const uint32_t n2 = tpair<0>(s2, lc.c0) ^ tpair<2>(s0, lc.c2) ^ rk[4 * r + 2] ^ r8(tpair<1>(s3, lc.c0) ^ tpair<3>(s1, lc.c2));
+    const uint32_t n3 = tpair<0>(s3, lc.c0) ^ tpair<2>(s1, lc.c2) ^ rk[4 * r + 3] ^ r8(tpair<1>(s0, lc.c0) ^ tpair<3>(s2, lc.c2));
+    s0 = n0;
+    s1 = n1;
+    s2 = n2;
+    s3 = n3;
+  }
+  // output byte r of column c = S[byte r of column c + r]: bytes 0 and 3 from T2, 1 and 2 from T0
+  auto last = [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    const uint32_t lo = __byte_perm(tpair<0>(a, lc.c2), tpair<1>(b, lc.c0), 0x3250u);
+    const uint32_t hi = __byte_perm(tpair<2>(c, lc.c0), tpair<3>(d, lc.c2), 0x7210u);
+    return __byte_perm(lo, hi, 0x7610u);
+  };
+  s[0] = last(s0, s1, s2, s3) ^ rk[40];
+  s[1] = last(s1, s2, s3, s0) ^ rk[41];
+  s[2] = last(s2, s3, s0, s1) ^ rk[42];
+  s[3] = last(s3, s0, s1, s2) ^ rk[43];
+}
+
 // aes128_encrypt on M independent blocks, their rounds interleaved (the same four shared
 // T-tables): a thread with M blocks overlaps their table-lookup latencies.
 template <int M>

@@ -44,28 +44,38 @@
 
 namespace fds {
 
-// one group's area
+// one group's area, in two parts: the large one (pixel tiles and staging) and the small one
+// (near-tie list, tile slots, counters)
 constexpr int kSmemPix = 0;                                  // 2 pixel tiles
 constexpr int kSmemStage = kSmemPix + 2 * kPixBytes;         // 1 staging area
-constexpr int kSmemQueue = kSmemStage + kCoefBytes;          // near-tie queue
+constexpr int kBigBytes = kSmemStage + kCoefBytes;
+constexpr int kSmemQueue = 0;                                // near-tie list
 constexpr int kDeferCap = 192;                               // recorded near ties per group
 constexpr int kSmemSlot = kSmemQueue + 8 * kDeferCap;        // 3 tile slots (ring)
 constexpr int kSlotBytes = (sizeof(TileSlot) + 15) & ~15;
 constexpr int kSmemMisc = kSmemSlot + 3 * kSlotBytes;
-constexpr int kGroupBytes = kSmemMisc + 32;
-// One image: one CTA per SM of three groups, then the AES table they share (T0 replicated
-// per lane).  Batches: up to four CTAs per SM of one group each, with the four 1 KB T-tables
-// after its area (a batch's tiles mostly carry little keystream -- k = 0: 24 blocks a tile).
+constexpr int kSmallBytes = (kSmemMisc + 32 + 127) & ~127;
+// One image: one CTA per SM of three groups and the AES pair table they share (64 KB at
+// shared-window address kTpairWin = 64 KB).  The window is laid out around the table: below
+// it the large part of group 0 and the small parts of all groups, above it the large parts
+// of groups 1 and 2; the dynamic area must start at or below kPreWin (it starts at 1 KB, after
+// the memory the hardware reserves for each CTA) and reach kEndWin.
+// Batches: up to four CTAs per SM of one group each, the large part, the small part and the
+// four 1 KB T-tables one after the other (a batch's tiles mostly carry little keystream --
+// k = 0: 24 blocks a tile).
+constexpr int kPreWin = (int)((kTpairWin - kBigBytes - 3 * kSmallBytes) & ~127u);
+constexpr int kEndWin = (int)kTpairWin + kTpairBytes + 2 * kBigBytes;
 template <bool BATCH>
 struct PLayout {
   static constexpr int kGroups = BATCH ? 1 : 3;
   static constexpr int kCtasPerSm = BATCH ? 4 : 1;
   static constexpr bool kSharedT = !BATCH;
-  static constexpr int kGroupStride = kGroupBytes + (kSharedT ? 0 : 4096);
-  static constexpr int kT = kSharedT ? kGroups * kGroupStride : kGroupBytes;   // CTA / group offset
-  static constexpr int kBytes = kGroups * kGroupStride + (kSharedT ? 4 * kTrepWords : 0);
+  // batches: the group's T-tables after its two parts
+  static constexpr int kT = kBigBytes + kSmallBytes;
+  static constexpr int kBytes = kSharedT ? kEndWin : kT + 4096;
 };
-static_assert(kGroupBytes % 16 == 0 && PLayout<false>::kBytes <= 227 * 1024 && PLayout<true>::kBytes <= 227 * 1024,
+static_assert(kBigBytes % 128 == 0 && kPreWin >= 2048 && kPreWin + kBigBytes + 3 * kSmallBytes <= (int)kTpairWin &&
+                  PLayout<false>::kBytes <= 227 * 1024 && PLayout<true>::kBytes <= 227 * 1024,
               "protect shared memory");
 
 // the public / private fragment staged for slot sl (staging area st) to global memory, one
@@ -322,29 +332,41 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
   using L = PLayout<BATCH>;
   constexpr int kPGroups = L::kGroups;
   extern __shared__ __align__(128) uint8_t smem_cta[];
-  if constexpr (L::kSharedT) {   // T0 replicated per lane, shared by the groups
-    uint32_t* T = reinterpret_cast<uint32_t*>(smem_cta + L::kT);
-    for (int i = threadIdx.x; i < kTrepWords; i += kThreads * kPGroups) T[i] = __ldg(a.T + (i >> 5));
-  } else {                       // each group's four T-tables
-    for (int i = threadIdx.x; i < kPGroups * 1024; i += kThreads * kPGroups)
-      reinterpret_cast<uint32_t*>(smem_cta + (i >> 10) * L::kGroupStride + L::kT)[i & 1023] = a.T[i & 1023];
-  }
-  __syncthreads();
-  // this thread's tile group: index, thread index in it, place among all groups of the launch
+  // shared-window address of the dynamic area, and this thread's tile group
+  const uint32_t win0 = smem_u32(smem_cta);
   const int grp = (int)threadIdx.x / kThreads;
   const int t = (int)threadIdx.x - grp * kThreads;
+  uint8_t* gbig;     // the group's pixel tiles and staging area
+  uint8_t* gsmall;   // its near-tie list, tile slots and counters
+  const uint32_t* Ts = nullptr;   // batches: the group's four T-tables
+  if constexpr (L::kSharedT) {
+    // the layout needs the dynamic area to start at or below kPreWin; elsewhere (never on
+    // sm_103a) the launch records a failure and does nothing
+    if (win0 > (uint32_t)kPreWin) {
+      if (threadIdx.x == 0 && a.counters) atomicAdd(&a.counters[2], 1ull);
+      return;
+    }
+    fill_pair_table(smem_cta + (kTpairWin - win0), a.T, (int)threadIdx.x, kThreads * kPGroups);
+    gbig = smem_cta + ((grp == 0 ? (uint32_t)kPreWin : kTpairWin + kTpairBytes + (grp - 1) * kBigBytes) - win0);
+    gsmall = smem_cta + ((uint32_t)(kPreWin + kBigBytes + grp * kSmallBytes) - win0);
+  } else {                       // each group's four T-tables
+    for (int i = threadIdx.x; i < kPGroups * 1024; i += kThreads * kPGroups)
+      reinterpret_cast<uint32_t*>(smem_cta + (i >> 10) * L::kBytes + L::kT)[i & 1023] = a.T[i & 1023];
+    gbig = smem_cta + grp * L::kBytes;
+    gsmall = gbig + kBigBytes;
+    Ts = reinterpret_cast<const uint32_t*>(gbig + L::kT);
+  }
+  __syncthreads();
   const int ng = a.groups >= 1 && a.groups < kPGroups ? a.groups : kPGroups;
   if (grp >= ng) return;
   const int vb = (int)blockIdx.x * ng + grp, vgrid = (int)gridDim.x * ng;
   const int gbar = 1 + grp;
-  uint8_t* smem = smem_cta + grp * L::kGroupStride;
-  const uint32_t* Ts = reinterpret_cast<const uint32_t*>(L::kSharedT ? smem_cta + L::kT : smem + L::kT);
-  uint2* deferred = reinterpret_cast<uint2*>(smem + kSmemQueue);   // near ties, after the tile loop
+  uint2* deferred = reinterpret_cast<uint2*>(gsmall + kSmemQueue);   // near ties, after the tile loop
   // misc: [0] queue size, [1] queued total, [2] escalations, [3] failures, [4..5] schedule
-  int* misc = reinterpret_cast<int*>(smem + kSmemMisc);
+  int* misc = reinterpret_cast<int*>(gsmall + kSmemMisc);
   const int ntiles = a.images ? a.total_tiles : (a.nblocks + kTileBlocks - 1) / kTileBlocks;
   if (vb >= ntiles) return;
-  auto slot = [&](int i) { return reinterpret_cast<TileSlot*>(smem + kSmemSlot + i * kSlotBytes); };
+  auto slot = [&](int i) { return reinterpret_cast<TileSlot*>(gsmall + kSmemSlot + i * kSlotBytes); };
 
   if (t < 4) misc[t] = 0;
   if (t == 0) {
@@ -353,7 +375,7 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
   }
   if (t < kTileBlocks) fill_slot(a, vb, slot(0), t);
   group_sync(gbar);
-  load_pixels(slot(0), smem + kSmemPix, t);
+  load_pixels(slot(0), gbig + kSmemPix, t);
 
   int it = 0;
   bool have_prev = false;
@@ -369,10 +391,10 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
     group_sync(gbar);                                                       // A
     if (t == 0) misc[4 + buf] = nxt < ntiles ? next_tile(a, it + 2, vb, vgrid) : ntiles;
     if constexpr (PACK != 0) {
-      if (have_prev) store_private_packed<PACK>(slot(s_prev), smem + kSmemStage, t);
+      if (have_prev) store_private_packed<PACK>(slot(s_prev), gbig + kSmemStage, t);
       if (t == 0) bulk_wait_read_all();      // the staging area may be written again
     } else if (!DEBUG && t == 0 && have_prev) {
-      store_private(slot(s_prev), smem + kSmemStage);   // the public part left before its AES
+      store_private(slot(s_prev), gbig + kSmemStage);   // the public part left before its AES
       bulk_wait_read_all();                  // the staging area may be written again
     }
     group_sync(gbar);                                                       // A'
@@ -400,14 +422,14 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
       }
     }
 
-    if (nxt < ntiles) load_pixels(slot(s_nxt), smem + kSmemPix + (buf ^ 1) * kPixBytes, t);
+    if (nxt < ntiles) load_pixels(slot(s_nxt), gbig + kSmemPix + (buf ^ 1) * kPixBytes, t);
 
     const int k = K >= 0 ? K : sl->k;
     const int npub = 63 - k;
     const int nb = sl->nb;
-    const uint8_t* tile_px = smem + kSmemPix + buf * kPixBytes;
-    int16_t* pubst = reinterpret_cast<int16_t*>(smem + kSmemStage);
-    int16_t* privst = reinterpret_cast<int16_t*>(smem + kSmemStage + kTileCb * 2 * npub);
+    const uint8_t* tile_px = gbig + kSmemPix + buf * kPixBytes;
+    int16_t* pubst = reinterpret_cast<int16_t*>(gbig + kSmemStage);
+    int16_t* privst = reinterpret_cast<int16_t*>(gbig + kSmemStage + kTileCb * 2 * npub);
     const int cb = t, b = t / 3, c = t - 3 * (t / 3);
     if (b < nb) {
       // row outputs kept as pairs of columns (0, 4), (1, 2), (3, 5), (6, 7), so that the
@@ -536,23 +558,23 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
     }
     if constexpr (PACK != 0) {
       group_sync(gbar);                                 // every staged coefficient is final
-      pack_tile<PACK>(smem + kSmemStage, nb, k, t, gbar);
+      pack_tile<PACK>(gbig + kSmemStage, nb, k, t, gbar);
     }
     fence_proxy_async();                   // every thread's staging writes, before the bulk store
     group_sync(gbar);                                                       // C
     if constexpr (PACK != 0) {
-      store_public_packed<PACK>(sl, smem + kSmemStage, t);   // it leaves during the AES
+      store_public_packed<PACK>(sl, gbig + kSmemStage, t);   // it leaves during the AES
       uint64_t off;
       int bytes;
       packed_extent<PACK>(sl, true, off, bytes);
-      ctr_tile_packed<L::kSharedT ? 7 : 0>(reinterpret_cast<uint32_t*>(privst), off, bytes, sl, a.rk, Ts, t);
+      ctr_tile_packed<L::kSharedT ? kTabPair : 0>(reinterpret_cast<uint32_t*>(privst), off, bytes, sl, a.rk, Ts, t);
     } else {
-      if (t == 0) store_public(sl, smem + kSmemStage);   // final: it leaves during the AES
+      if (t == 0) store_public(sl, gbig + kSmemStage);   // final: it leaves during the AES
       if (!a.plain_private)
       {
         const uint64_t first = ((uint64_t)sl->local * kTileBlocks * 6ull * (uint64_t)(k + 1)) >> 4;
         if constexpr (L::kSharedT)
-          ctr_tile_rep<7>(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1), first, sl, a.rk, Ts, false, t);
+          ctr_tile_pair(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1), first, sl, a.rk, t);
         else
           ctr_tile(reinterpret_cast<uint8_t*>(privst), nb * 6 * (k + 1), first, sl, sl->rk, Ts, a.aes_pair, t);
       }
@@ -563,10 +585,10 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
   if (DEBUG) return;
   group_sync(gbar);
   if constexpr (PACK != 0) {
-    if (have_prev) store_private_packed<PACK>(slot((it + 2) % 3), smem + kSmemStage, t);
+    if (have_prev) store_private_packed<PACK>(slot((it + 2) % 3), gbig + kSmemStage, t);
   }
   if (t == 0) {
-    if (PACK == 0 && have_prev) store_private(slot((it + 2) % 3), smem + kSmemStage);
+    if (PACK == 0 && have_prev) store_private(slot((it + 2) % 3), gbig + kSmemStage);
     bulk_wait_all();
     asm volatile("fence.proxy.async.global;\n" ::: "memory");   // bulk writes, then the patches
   }
@@ -577,7 +599,7 @@ __global__ void __launch_bounds__(kThreads * PLayout<BATCH>::kGroups, PLayout<BA
     bool fail = false;
     // packed-stream patches are applied by one thread (fields share bytes; the pixel tiles are
     // free now and hold them); patches never cross into another tile's bytes or CTA
-    BitPatch* bp = reinterpret_cast<BitPatch*>(smem + kSmemPix);
+    BitPatch* bp = reinterpret_cast<BitPatch*>(gbig + kSmemPix);
     for (int i = t; i < nd; i += kThreads) resolve_deferred<BATCH, PACK>(a, deferred[i], &esc, &fail, bp + i);
     if constexpr (PACK != 0) {
       group_sync(gbar);

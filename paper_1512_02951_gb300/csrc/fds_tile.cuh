@@ -402,6 +402,26 @@ __device__ __forceinline__ void ctr_tile_rep(uint8_t* st, int bytes, uint64_t fi
   }
 }
 
+// ctr_tile with the pair table (window address kTpairWin, see aes128_encrypt_pair), one
+// keystream block per thread; t = the thread's index in its 192-thread tile group.
+__device__ __forceinline__ void ctr_tile_pair(uint8_t* st, int bytes, uint64_t first_block, const TileSlot* sl,
+                                              const uint32_t* rk, int t) {
+  const int nblk = (bytes + 15) >> 4;
+  const PairLanes lc = pair_lanes();
+  for (int i = t; i < nblk; i += kThreads) {
+    uint32_t s[4];
+    ctr_block(sl->iv_hi, sl->iv_lo, first_block + i, s);
+    aes128_encrypt_pair(s, rk, lc);
+    uint4* p = reinterpret_cast<uint4*>(st + 16 * i);
+    uint4 d = *p;
+    d.x ^= s[0];
+    d.y ^= s[1];
+    d.z ^= s[2];
+    d.w ^= s[3];
+    *p = d;
+  }
+}
+
 // ---- packed storage (Sect. 6.4.3): a full tile's 192 channel-blocks are a multiple of 8,
 // so its part of either bit stream starts on a byte boundary
 constexpr int kDcBits = 11;
@@ -419,7 +439,9 @@ __device__ __forceinline__ void packed_extent(const TileSlot* sl, bool priv, uin
 // AES-128-CTR over the tile's packed private part (words at w, stream bytes [off, off +
 // bytes), off a multiple of 4): one thread per keystream block the part overlaps; a block
 // that straddles two tiles is generated by both, each XORing its own words
-// SH = 0: the four T-tables at Ts, else a replicated T0 as in ctr_tile_rep
+// SH = 0: the four T-tables at Ts; SH = kTabPair: the pair table (Ts unused); else a
+// replicated T0 as in ctr_tile_rep
+constexpr int kTabPair = -1;
 template <int SH = 0>
 __device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int bytes, const TileSlot* sl,
                                                 const uint32_t* rk, const uint32_t* Ts, int t) {
@@ -427,11 +449,14 @@ __device__ __forceinline__ void ctr_tile_packed(uint32_t* w, uint64_t off, int b
   const int nblk = (int)(((off + (uint64_t)bytes + 15) >> 4) - b0);
   const int nw = (bytes + 3) >> 2;
   const int skew = (int)((off & 15) >> 2);
-  const uint32_t Tl = SH ? smem_u32(Ts) + 4u * (t & ((1 << (SH > 2 ? SH - 2 : 0)) - 1)) : 0u;
+  const uint32_t Tl = SH > 0 ? smem_u32(Ts) + 4u * (t & ((1 << (SH > 2 ? SH - 2 : 0)) - 1)) : 0u;
+  const PairLanes lc = pair_lanes();
   for (int i = t; i < nblk; i += kThreads) {
     uint32_t s[4];
     ctr_block(sl->iv_hi, sl->iv_lo, b0 + i, s);
-    if constexpr (SH != 0)
+    if constexpr (SH == kTabPair)
+      aes128_encrypt_pair(s, rk, lc);
+    else if constexpr (SH != 0)
       aes128_encrypt_rep<SH>(s, rk, Tl);
     else
       aes128_encrypt(s, rk, Ts);
