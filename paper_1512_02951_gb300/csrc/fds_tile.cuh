@@ -128,8 +128,8 @@ struct TileSlot {
 constexpr int32_t kPxIn16 = 1, kPxOut16 = 2;
 
 // launchers (one translation unit each); `sms` = number of SMs of the device, `per_sm` =
-// CTAs per SM to launch, at most the kernel's residency (protect 4, restore 2); 0 = that
-// residency
+// tile groups per SM to launch, at most the kernel's residency (protect: 3 groups of one CTA
+// for one image, 4 CTAs for batches; restore: 2 CTAs); 0 = that residency
 cudaError_t launch_protect(const TileArgs& a, cudaStream_t s, bool debug, int sms, int per_sm = 0);
 cudaError_t launch_restore(const TileArgs& a, cudaStream_t s, int sms, int per_sm = 0);
 // restore with the inverse transform on tensor cores (one image, int16 storage)
