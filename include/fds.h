@@ -499,6 +499,19 @@ int fds_debug_set_counters(const uint64_t* values);
 /* Message describing the calling thread's last error ("" if none). */
 const char* fds_last_error(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Copies of a serving batch (the paper has no counterpart: a host-side helper of the serving
+ * loop).  Enqueues n asynchronous copies on `stream`, in order: copy i moves bytes[i] bytes
+ * from address srcs[i] to address dsts[i].  Addresses are host or device pointers given as
+ * integers (host arrays of n each, read before the call returns); the direction of each copy
+ * follows from its addresses (unified addressing), and host memory should be pinned for the
+ * copy to overlap other work.  One cudaMemcpyAsync per copy: a batch's inputs and outputs
+ * move with one call instead of one call per request.  Copies of 0 bytes are skipped.
+ * Errors: n < 0, a null array with n > 0, or a null address of a non-empty copy ->
+ * FDS_E_INVALID; a copy the runtime refuses -> FDS_E_CUDA (the copies before it stay
+ * enqueued). */
+int fds_copy_many(const uint64_t* dsts, const uint64_t* srcs, const uint64_t* bytes, int32_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

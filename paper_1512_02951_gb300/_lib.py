@@ -148,6 +148,8 @@ SIGNATURES = {
     "fds_status_of_failures": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64]),
     "fds_debug_set_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "fds_last_error": (ctypes.c_char_p, []),
+    "fds_copy_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -173,6 +173,61 @@ def layout(descs: Sequence[ImageDesc]) -> tuple[int, int, int]:
     return px, pub, priv
 
 
+# struct fds_image as a numpy record (the same 56 bytes as _lib.FdsImage)
+FDS_IMAGE_DTYPE = None
+
+
+def fds_image_dtype():
+    global FDS_IMAGE_DTYPE
+    if FDS_IMAGE_DTYPE is None:
+        import numpy as np
+        FDS_IMAGE_DTYPE = np.dtype([("pixel_offset", "<u8"), ("public_offset", "<u8"), ("private_offset", "<u8"),
+                                    ("width", "<i4"), ("height", "<i4"), ("k", "<i4"), ("key_slot", "<i4"),
+                                    ("iv", "u1", (16,))])
+        assert FDS_IMAGE_DTYPE.itemsize == ctypes.sizeof(_lib.FdsImage)
+    return FDS_IMAGE_DTYPE
+
+
+def layout_arrays(pixel_bytes, public_bytes, private_bytes):
+    """layout() over arrays of per-image sizes (numpy int64): the (pixel, public, private)
+    offsets, packed as layout() packs them (pixels 8-aligned, fragments 16-aligned), and the
+    three buffer sizes."""
+    import numpy as np
+    out = []
+    for b, a in ((pixel_bytes, 7), (public_bytes, 15), (private_bytes, 15)):
+        step = (np.asarray(b, dtype=np.int64) + a) & ~a
+        end = np.cumsum(step)
+        out.append((end - step, int(end[-1]) if len(end) else 0))
+    return tuple(o for o, _ in out), tuple(t for _, t in out)
+
+
+def desc_records(widths, heights, ks, key_slots, ivs, offsets):
+    """The fds_image descriptors of a batch as one numpy record array: per-image fields as
+    sequences, ivs as 16-byte strings, offsets as returned by layout_arrays."""
+    import numpy as np
+    n = len(widths)
+    rec = np.zeros(n, dtype=fds_image_dtype())
+    rec["pixel_offset"], rec["public_offset"], rec["private_offset"] = offsets
+    rec["width"], rec["height"], rec["k"], rec["key_slot"] = widths, heights, ks, key_slots
+    if n:
+        rec["iv"] = np.frombuffer(b"".join(_check_key(v, "iv") for v in ivs), dtype=np.uint8).reshape(n, 16)
+    return rec
+
+
+def copy_many(dsts, srcs, nbytes, stream: torch.cuda.Stream | None = None) -> None:
+    """fds_copy_many: copy i moves nbytes[i] bytes from address srcs[i] to address dsts[i]
+    (host or device pointers as integers), all enqueued on `stream` by one call."""
+    import numpy as np
+    d = np.ascontiguousarray(dsts, dtype=np.uint64)
+    s_ = np.ascontiguousarray(srcs, dtype=np.uint64)
+    b = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    if not (len(d) == len(s_) == len(b)):
+        raise ValueError("copy_many: dsts, srcs and nbytes differ in length")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _lib.check(_lib.load().fds_copy_many(d.ctypes.data, s_.ctypes.data, b.ctypes.data, len(d), st),
+               "fds_copy_many")
+
+
 def _desc_array(descs: Sequence[ImageDesc]):
     arr = (_lib.FdsImage * max(1, len(descs)))()
     for i, d in enumerate(descs):
@@ -543,6 +598,15 @@ class Plan:
         s = (stream or torch.cuda.current_stream()).cuda_stream
         _lib.check(_lib.load().fds_plan_update(self._h, arr, len(descs), s), "fds_plan_update")
         self.descs = list(descs)
+
+    def update_records(self, rec, stream: torch.cuda.Stream | None = None) -> None:
+        """fds_plan_update from a record array of desc_records (no ImageDesc objects)."""
+        import numpy as np
+        rec = np.ascontiguousarray(rec, dtype=fds_image_dtype())
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        ptr = ctypes.cast(rec.ctypes.data, ctypes.POINTER(_lib.FdsImage))
+        _lib.check(_lib.load().fds_plan_update(self._h, ptr, len(rec), s), "fds_plan_update")
+        self.descs = None
 
     def close(self) -> None:
         if self._h:

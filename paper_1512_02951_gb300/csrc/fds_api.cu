@@ -1345,6 +1345,18 @@ int fds_sync(void* stream) {
 
 const char* fds_last_error(void) { return t_err.c_str(); }
 
+int fds_copy_many(const uint64_t* dsts, const uint64_t* srcs, const uint64_t* bytes, int32_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!dsts || !srcs || !bytes))) return set_err(FDS_E_INVALID, "fds_copy_many: bad arguments");
+  for (int32_t i = 0; i < n; ++i) {
+    if (!bytes[i]) continue;
+    if (!dsts[i] || !srcs[i]) return set_err(FDS_E_INVALID, "fds_copy_many: null address in copy " + std::to_string(i));
+    const cudaError_t e = cudaMemcpyAsync(reinterpret_cast<void*>(dsts[i]), reinterpret_cast<const void*>(srcs[i]),
+                                          (size_t)bytes[i], cudaMemcpyDefault, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, ("fds_copy_many: copy " + std::to_string(i)).c_str());
+  }
+  return FDS_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------

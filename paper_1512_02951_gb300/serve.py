@@ -11,9 +11,9 @@ on the device (key slots); every request names its slot and its own initial coun
 
 Host side: inputs that are not pinned host tensors are copied into pinned memory by a pool of
 staging threads when they are submitted (off the scheduler thread); a batch's outputs leave the
-device as one copy per fragment buffer into the lane's pinned host buffers, from which the
-same pool copies each request's result out (the lane takes its next batch once they are
-out).  The lane's device and pinned host buffers persist and grow with the largest batch, so
+device as one copy per fragment buffer into the lane's pinned host buffers, which the same pool
+copies out once per batch (the lane takes its next batch once they are out); each request's
+result is a view into that copy.  The lane's device and pinned host buffers persist and grow with the largest batch, so
 a warm server allocates no pinned memory.
 
 Each result is bit-for-bit what the request gives alone: batching changes only which launch
@@ -36,8 +36,8 @@ import numpy as np
 @dataclass
 class Request:
     """One protect request (``pixels`` H x W x 3 uint8) or restore request (``public`` int16
-    fragment bytes and ``private`` ciphertext bytes).  Host arrays; pinned memory is copied
-    faster."""
+    fragment bytes and ``private`` ciphertext bytes).  Host arrays or tensors of exactly those
+    sizes; pinned memory is copied faster."""
     kind: str                      # "protect" or "restore"
     width: int
     height: int
@@ -47,6 +47,10 @@ class Request:
     pixels: object = None          # protect input
     public: object = None          # restore inputs
     private: object = None
+    # optional output buffers the result is copied into straight from the device (contiguous
+    # CPU tensors, pinned for speed, each at least the result's bytes): protect (public,
+    # private), restore (pixels,); the result is then given as arrays over them
+    out: tuple = None
     arrival: float = 0.0           # time.perf_counter() at submission
     done: float = 0.0              # time.perf_counter() when the result was ready
     future: Future = field(default_factory=Future)
@@ -113,45 +117,78 @@ class GpuLane:
     def launch(self, batch: list[Request]) -> None:
         torch, api = self.torch, self.api
         kind = batch[0].kind
-        descs = [api.ImageDesc(r.width, r.height, r.k, r.key_slot, r.iv) for r in batch]
-        npx, npub, npriv = api.layout(descs)
+        # per-request sizes, offsets and descriptors, as arrays (no per-request objects)
+        sz = np.array([r.sizes() for r in batch], dtype=np.int64).reshape(-1, 3)
+        offs, (npx, npub, npriv) = api.layout_arrays(sz[:, 0], sz[:, 1], sz[:, 2])
+        rec = api.desc_records([r.width for r in batch], [r.height for r in batch], [r.k for r in batch],
+                               [r.key_slot for r in batch], [r.iv for r in batch], offs)
+        self.nbytes, self.offs = (npx, npub, npriv), offs
+        refs = []                                   # host inputs, alive until the batch is over
         with torch.cuda.stream(self.stream):
             dev = dict(device=self.device)
             px, pub, priv = (self._grow(self.bufs, 0, npx, **dev), self._grow(self.bufs, 1, npub, **dev),
                              self._grow(self.bufs, 2, npriv, **dev))
-            for r, d in zip(batch, descs):
-                n, pb, vb = r.sizes()
-                ins = r.inputs()
-                if kind == "protect":
-                    px[d.pixel_offset: d.pixel_offset + n].copy_(_host_u8(torch, ins[0]), non_blocking=True)
-                else:
-                    pub[d.public_offset: d.public_offset + pb].copy_(_host_u8(torch, ins[0]), non_blocking=True)
-                    priv[d.private_offset: d.private_offset + vb].copy_(_host_u8(torch, ins[1]), non_blocking=True)
-            self.plan.update(descs, self.stream)
+            # every input of the batch by one call, one copy each
+            if kind == "protect":
+                api.copy_many(px.data_ptr() + offs[0].astype(np.uint64),
+                              [_host_ptr(torch, r.inputs()[0], refs) for r in batch], sz[:, 0], self.stream)
+            else:
+                dsts = np.concatenate([pub.data_ptr() + offs[1].astype(np.uint64),
+                                       priv.data_ptr() + offs[2].astype(np.uint64)])
+                srcs = [_host_ptr(torch, r.inputs()[0], refs) for r in batch] + \
+                       [_host_ptr(torch, r.inputs()[1], refs) for r in batch]
+                api.copy_many(dsts, srcs, np.concatenate([sz[:, 1], sz[:, 2]]), self.stream)
+            self.plan.update_records(rec, self.stream)
             if kind == "protect":
                 self.plan.protect(px, pub, priv)
-                h0 = self._grow(self.hbufs, 0, npub, pin_memory=True)
-                h1 = self._grow(self.hbufs, 1, npriv, pin_memory=True)
-                h0[:npub].copy_(pub[:npub], non_blocking=True)
-                h1[:npriv].copy_(priv[:npriv], non_blocking=True)
             else:
                 self.plan.restore(pub, priv, px)
-                h0 = self._grow(self.hbufs, 0, npx, pin_memory=True)
-                h0[:npx].copy_(px[:npx], non_blocking=True)
+            # results: straight into the buffers of the requests that brought them, the rest
+            # into the lane's pinned buffers
+            direct = np.array([r.out is not None for r in batch], dtype=bool)
+            if direct.any():
+                idx = np.nonzero(direct)[0]
+                if kind == "protect":
+                    dsts = [r.out[0].data_ptr() for r in batch if r.out is not None] + \
+                           [r.out[1].data_ptr() for r in batch if r.out is not None]
+                    srcs = np.concatenate([pub.data_ptr() + offs[1][idx].astype(np.uint64),
+                                           priv.data_ptr() + offs[2][idx].astype(np.uint64)])
+                    api.copy_many(dsts, srcs, np.concatenate([sz[idx, 1], sz[idx, 2]]), self.stream)
+                else:
+                    api.copy_many([r.out[0].data_ptr() for r in batch if r.out is not None],
+                                  px.data_ptr() + offs[0][idx].astype(np.uint64), sz[idx, 0], self.stream)
+            if not direct.all():
+                if kind == "protect":
+                    h0 = self._grow(self.hbufs, 0, npub, pin_memory=True)
+                    h1 = self._grow(self.hbufs, 1, npriv, pin_memory=True)
+                    h0[:npub].copy_(pub[:npub], non_blocking=True)
+                    h1[:npriv].copy_(priv[:npriv], non_blocking=True)
+                else:
+                    h0 = self._grow(self.hbufs, 0, npx, pin_memory=True)
+                    h0[:npx].copy_(px[:npx], non_blocking=True)
             self.event = torch.cuda.Event()
             self.event.record(self.stream)
-        self.batch, self.hold = batch, descs
+        self.batch, self.hold = batch, refs
 
     def finish(self) -> list[tuple[Request, object]]:
-        """One (request, builder) per request of the finished batch; builder() returns the
-        result copied out of the pinned buffers: protect -> (public int16 array
-        [H/8, W/8, 3, 63-k], private bytes); restore -> H x W x 3 uint8 array.  Call release()
-        after every builder has run."""
+        """One (request, result or builder) per request of the finished batch: protect ->
+        (public int16 array [H/8, W/8, 3, 63-k], private bytes); restore -> H x W x 3 uint8
+        array.  A request that brought its own output buffers gets its result at once, as
+        arrays over those buffers; for the others builder() returns a view into one copy of
+        the lane's pinned buffers.  Call release() after every builder has run."""
         self.draining = True
-        host = [h.numpy() if h is not None else None for h in self.hbufs]
+        if self.batch[0].kind == "protect":
+            used = [self.nbytes[1], self.nbytes[2]]
+        else:
+            used = [self.nbytes[0], 0]
+        host = _BatchCopy(self.hbufs, used)
         out = []
-        for r, d in zip(self.batch, self.hold):
-            out.append((r, functools.partial(_result_of, r, d, host)))
+        for i, r in enumerate(self.batch):
+            o = (int(self.offs[0][i]), int(self.offs[1][i]), int(self.offs[2][i]))
+            if r.out is not None:
+                out.append((r, _result_in(r)))
+            else:
+                out.append((r, functools.partial(_result_of, r, o, host)))
         return out
 
     def release(self) -> None:
@@ -162,14 +199,89 @@ class GpuLane:
         self.plan.close()
 
 
-def _result_of(r: Request, d, host):
-    """Request r's result copied out of the lane's pinned host buffers `host` (numpy views)."""
+class _BatchCopy:
+    """The used part of a lane's pinned output buffers, copied once per batch into ordinary host
+    memory by whichever result builder runs first (a torch clone: it runs without the
+    interpreter lock); every request's result is then a view into that copy, which stays alive
+    as long as one of them does."""
+
+    def __init__(self, bufs, used):
+        self.bufs, self.used = bufs, used
+        self.lock = threading.Lock()
+        self.copy = None
+
+    def get(self):
+        with self.lock:
+            if self.copy is None:
+                self.copy = [b[:n].clone() if (b is not None and n) else None for b, n in zip(self.bufs, self.used)]
+        return self.copy
+
+
+def _result_of(r: Request, offs, batch_copy: _BatchCopy):
+    """Request r's result as a view into its batch's copy of the lane's output buffers; offs =
+    its (pixel, public, private) offsets in the batch."""
+    host = batch_copy.get()
     n, pb, vb = r.sizes()
     if r.kind == "protect":
-        pub = np.array(host[0][d.public_offset: d.public_offset + pb]).view(np.int16).reshape(
-            r.height // 8, r.width // 8, 3, 63 - r.k)
-        return pub, host[1][d.private_offset: d.private_offset + vb].tobytes()
-    return np.array(host[0][d.pixel_offset: d.pixel_offset + n]).reshape(r.height, r.width, 3)
+        pub = host[0][offs[1]: offs[1] + pb].numpy().view(np.int16).reshape(r.height // 8, r.width // 8, 3, 63 - r.k)
+        return pub, host[1][offs[2]: offs[2] + vb].numpy().tobytes()
+    return host[0][offs[0]: offs[0] + n].numpy().reshape(r.height, r.width, 3)
+
+
+def _u8(t):
+    """A contiguous CPU tensor's bytes as a numpy uint8 array (no copy)."""
+    return t.numpy().reshape(-1).view(np.uint8)
+
+
+def _result_in(r: Request):
+    """The result of a request that brought its own output buffers, over those buffers."""
+    n, pb, vb = r.sizes()
+    if r.kind == "protect":
+        pub = _u8(r.out[0])[:pb].view(np.int16).reshape(r.height // 8, r.width // 8, 3, 63 - r.k)
+        return pub, _u8(r.out[1])[:vb].tobytes()
+    return _u8(r.out[0])[:n].reshape(r.height, r.width, 3)
+
+
+def _host_ptr(torch, a, refs: list) -> int:
+    """Address of input `a` (a contiguous tensor, a numpy array or bytes); `a`, or the
+    contiguous copy whose address this is, is appended to refs."""
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        refs.append(a)
+        return a.data_ptr()
+    if isinstance(a, (bytes, bytearray, memoryview)):
+        arr = np.frombuffer(a, dtype=np.uint8)
+    else:
+        arr = np.ascontiguousarray(a)
+    refs.append(arr)
+    return arr.ctypes.data
+
+
+def _check_buffers(req: Request) -> None:
+    """Inputs of exactly the request's sizes; output buffers (if any) large enough."""
+    import torch
+    n, pb, vb = req.sizes()
+    need = (n,) if req.kind == "protect" else (pb, vb)
+    for i, (a, b) in enumerate(zip(req.inputs(), need)):
+        if a is None or _nbytes(torch, a) != b:
+            raise ValueError(f"{req.kind} input {i}: {b} bytes expected")
+    if req.out is not None:
+        need = (pb, vb) if req.kind == "protect" else (n,)
+        if len(req.out) != len(need):
+            raise ValueError(f"{req.kind} takes {len(need)} output buffers")
+        for o, b in zip(req.out, need):
+            if not (isinstance(o, torch.Tensor) and o.device.type == "cpu" and o.is_contiguous()
+                    and _nbytes(torch, o) >= b):
+                raise ValueError(f"output buffers: contiguous CPU tensors of at least {need} bytes")
+
+
+def _nbytes(torch, a) -> int:
+    if isinstance(a, torch.Tensor):
+        return a.numel() * a.element_size()
+    if isinstance(a, (bytes, bytearray, memoryview)):
+        return len(a)
+    return int(np.asarray(a).nbytes)
 
 
 def _host_u8(torch, a):
@@ -236,6 +348,7 @@ class Server:
             raise ValueError("kind must be 'protect' or 'restore'")
         if req.device_bytes() > self.mem_budget:
             raise ValueError("request larger than the server's device-memory budget")
+        _check_buffers(req)
         req.arrival = time.perf_counter()
         if self._stager is not None and not self._pinned(req):
             with self._lock:

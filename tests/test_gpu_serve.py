@@ -91,3 +91,52 @@ def test_poisson_arrivals_report_latency(env):
     out = run_poisson(srv, reqs, synth.poisson_arrivals(len(reqs), 500.0, 23))
     srv.close()
     assert out["requests"] == 40 and 0 < out["p50_ms"] <= out["p99_ms"] < 5000
+
+
+def _with_outputs(r, pinned):
+    """A copy of request r that brings its own output buffers (pinned or pageable)."""
+    c = _clone(r)
+    n, pb, vb = c.sizes()
+    shapes = (pb, vb) if r.kind == "protect" else (n,)
+    c.out = tuple(torch.full((b + 5,), 0xA5, dtype=torch.uint8, pin_memory=pinned) for b in shapes)
+    return c
+
+
+def test_caller_output_buffers_give_the_same_results(env):
+    # requests that bring output buffers get their results straight from the device; in a
+    # mix with requests that do not, every result equals the one served the usual way
+    from paper_1512_02951_gb300.serve import Server
+    reqs = _make(env, 36, 31)
+    srv = Server(lanes=2, max_batch=12)
+    base = [_clone(r) for r in reqs]
+    for r in base:
+        srv.submit(r)
+    want = [r.future.result(timeout=120) for r in base]
+    mixed = [(_with_outputs(r, pinned=(i % 3 != 2)) if i % 4 != 3 else _clone(r)) for i, r in enumerate(reqs)]
+    for r in mixed:
+        srv.submit(r)
+    got = [r.future.result(timeout=120) for r in mixed]
+    srv.close()
+    for r, g, w in zip(mixed, got, want):
+        assert _equal(g, w), (r.kind, r.width, r.height, r.k)
+        if r.out is not None:                         # the result lies in the caller's buffer
+            n, pb, vb = r.sizes()
+            if r.kind == "protect":
+                assert g[0].ctypes.data == r.out[0].data_ptr()
+                assert r.out[0][pb:].eq(0xA5).all() and r.out[1][vb:].eq(0xA5).all()
+            else:
+                assert g.ctypes.data == r.out[0].data_ptr() and r.out[0][n:].eq(0xA5).all()
+
+
+def test_request_buffers_are_checked_at_submission(env):
+    from paper_1512_02951_gb300.serve import Request, Server
+    srv = Server(lanes=1, max_batch=4)
+    img = synth.make_image(16, 8, 3)
+    with pytest.raises(ValueError):                   # input of the wrong size
+        srv.submit(Request("protect", 16, 16, 0, env[2][0], synth.make_iv(1), pixels=img))
+    r = Request("protect", 16, 8, 0, env[2][0], synth.make_iv(1), pixels=img)
+    n, pb, vb = r.sizes()
+    r.out = (torch.empty(pb, dtype=torch.uint8), torch.empty(vb - 1, dtype=torch.uint8))
+    with pytest.raises(ValueError):                   # output buffer too small
+        srv.submit(r)
+    srv.close()

@@ -117,3 +117,37 @@ def test_restore_request_ciphertext_is_what_ctr_gives():
     r = reqs[0]
     plain = oaes.ctr_xcrypt(KEYS[r.key_slot], r.iv, r.private)
     assert len(plain) == ofds.sizes(r.width, r.height, r.k)[1]
+
+
+def test_vectorised_layout_and_descriptors_match_the_per_image_forms():
+    # the serving lane builds a batch's offsets and fds_image records as arrays; they must be
+    # byte for byte what layout() and the ctypes descriptor array give
+    from paper_1512_02951_gb300 import api
+    rng = np.random.default_rng(3)
+    descs = [api.ImageDesc(int(rng.integers(1, 40)) * 8, int(rng.integers(1, 40)) * 8, int(rng.choice([0, 5, 63])),
+                           int(rng.integers(0, 9)), bytes(rng.integers(0, 256, 16, dtype=np.uint8)))
+             for _ in range(50)]
+    totals = api.layout(descs)
+    sz = np.array([(d.width * d.height * 3,) + tuple(api.sizes(d.width, d.height, d.k)) for d in descs])
+    offs, tot = api.layout_arrays(sz[:, 0], sz[:, 1], sz[:, 2])
+    assert tot == totals
+    assert offs[0].tolist() == [d.pixel_offset for d in descs]
+    assert offs[1].tolist() == [d.public_offset for d in descs]
+    assert offs[2].tolist() == [d.private_offset for d in descs]
+    rec = api.desc_records([d.width for d in descs], [d.height for d in descs], [d.k for d in descs],
+                           [d.key_slot for d in descs], [d.iv for d in descs], offs)
+    assert rec.tobytes() == bytes(api._desc_array(descs))
+
+
+def test_copy_many_rejects_bad_arguments_on_the_host():
+    import ctypes
+    from paper_1512_02951_gb300 import _lib
+    lib = _lib.load()
+    one = (ctypes.c_uint64 * 1)(8)
+    zero = (ctypes.c_uint64 * 1)(0)
+    assert lib.fds_copy_many(None, None, None, 0, None) == _lib.FDS_OK          # nothing to copy
+    assert lib.fds_copy_many(None, None, None, -1, None) == _lib.FDS_E_INVALID
+    assert lib.fds_copy_many(None, one, one, 1, None) == _lib.FDS_E_INVALID     # null array
+    assert lib.fds_copy_many(zero, one, one, 1, None) == _lib.FDS_E_INVALID     # null address
+    assert b"null address" in lib.fds_last_error()
+    assert lib.fds_copy_many(zero, zero, zero, 1, None) == _lib.FDS_OK          # empty copies are skipped
