@@ -66,7 +66,16 @@ cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uin
                             const uint32_t rk[44], const uint32_t* T, cudaStream_t s, int sms,
                             unsigned long long* counters) {
   static bool attr[kMaxAttrDevices];
-  cudaError_t e = smem_attr_once(aes_ctr_full_kernel, kFullSmem, attr);
+  static bool window_ok[kMaxAttrDevices];
+  int dev = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxAttrDevices) return cudaErrorInvalidDevice;
+  if (!window_ok[dev]) {   // the pair table at window address 64 KB
+    if ((e = smem_window_start_ok(aes_ctr_full_kernel, kTpairWin)) != cudaSuccess) return e;
+    window_ok[dev] = true;
+  }
+  e = smem_attr_once(aes_ctr_full_kernel, kFullSmem, attr);
   if (e != cudaSuccess) return e;
   FullArgs a{};
   a.in = in;

@@ -7,6 +7,23 @@
 
 namespace fds {
 
+// Kernels that lay their shared memory out at fixed shared-window addresses need their dynamic
+// area to start at or below max_start.  The area starts after the memory the device reserves
+// for each CTA and the kernel's static shared memory (128-byte aligned); this checks that on
+// the current device (the kernels check it again and, should it ever fail there, count a
+// failure and do nothing).
+template <typename Kernel>
+inline cudaError_t smem_window_start_ok(Kernel kernel, uint32_t max_start) {
+  int dev = 0, reserved = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+  const size_t start = (size_t)reserved + ((fa.sharedSizeBytes + 127) & ~(size_t)127);
+  return start <= max_start ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
 // AES-128-CTR over a whole buffer (the full-encryption comparator); counters: the device's
 // three counters (the failure counter records a launch that could not place its table)
 cudaError_t launch_aes_full(const uint8_t* in, uint8_t* out, uint64_t bytes, uint64_t iv_hi, uint64_t iv_lo,

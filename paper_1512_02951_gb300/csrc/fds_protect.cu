@@ -40,6 +40,7 @@
 // stream order), and AES-128-CTR runs over the packed private bytes at their offset in the
 // image's private stream.  A full tile holds 192 channel-blocks, a multiple of 8, so every
 // tile's part of either stream starts on a byte boundary.
+#include "fds_aux.h"
 #include "fds_tile.cuh"
 
 namespace fds {
@@ -627,7 +628,18 @@ template <int K, bool DEBUG, bool BATCH, int PACK = 0>
 static cudaError_t launch_k(const TileArgs& a, cudaStream_t s, int sms, int per_sm) {
   static bool attr[kMaxAttrDevices];
   using L = PLayout<BATCH>;
-  cudaError_t e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, L::kBytes, attr);
+  static bool window_ok[kMaxAttrDevices];
+  cudaError_t e;
+  if constexpr (L::kSharedT) {   // the groups' areas and the pair table at fixed window addresses
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxAttrDevices) return cudaErrorInvalidDevice;
+    if (!window_ok[dev]) {
+      if ((e = smem_window_start_ok(protect_kernel<K, DEBUG, BATCH, PACK>, (uint32_t)kPreWin)) != cudaSuccess) return e;
+      window_ok[dev] = true;
+    }
+  }
+  e = smem_attr_once(protect_kernel<K, DEBUG, BATCH, PACK>, L::kBytes, attr);
   if (e != cudaSuccess) return e;
   const int ntiles = total_tiles(a);
   // per_sm: tile groups working on each SM (one image: groups of the one CTA; batches: CTAs)
