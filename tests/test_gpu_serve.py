@@ -140,3 +140,24 @@ def test_request_buffers_are_checked_at_submission(env):
     with pytest.raises(ValueError):                   # output buffer too small
         srv.submit(r)
     srv.close()
+
+
+def test_copy_many_moves_every_range(env):
+    # fds_copy_many on its own: host -> device, device -> host and device -> device ranges of
+    # uneven sizes (0 and 1 byte included) in one call each, on a side stream
+    from paper_1512_02951_gb300 import api
+    rng = np.random.default_rng(5)
+    sizes = [0, 1, 7, 16, 4099, 65536, 3, 1 << 20]
+    src = [torch.from_numpy(rng.integers(0, 256, n, dtype=np.uint8)).pin_memory() for n in sizes]
+    dev = torch.zeros(sum(sizes) + 64, dtype=torch.uint8, device="cuda")
+    offs = np.concatenate(([0], np.cumsum(sizes)[:-1])).astype(np.uint64)
+    s = torch.cuda.Stream()
+    api.copy_many(dev.data_ptr() + offs, [t.data_ptr() for t in src], sizes, s)
+    back = [torch.full((n,), 7, dtype=torch.uint8).pin_memory() for n in sizes]
+    api.copy_many([t.data_ptr() for t in back], dev.data_ptr() + offs, sizes, s)
+    dev2 = torch.zeros_like(dev)
+    api.copy_many(dev2.data_ptr() + offs, dev.data_ptr() + offs, sizes, s)
+    s.synchronize()
+    for a, b in zip(src, back):
+        assert torch.equal(a, b)
+    assert torch.equal(dev, dev2) and int(dev[sum(sizes):].sum()) == 0
