@@ -151,3 +151,43 @@ def test_copy_many_rejects_bad_arguments_on_the_host():
     assert lib.fds_copy_many(zero, one, one, 1, None) == _lib.FDS_E_INVALID     # null address
     assert b"null address" in lib.fds_last_error()
     assert lib.fds_copy_many(zero, zero, zero, 1, None) == _lib.FDS_OK          # empty copies are skipped
+
+
+def test_buffer_checks_and_result_views_on_the_host():
+    # the host side of caller output buffers and of the lane's result builders, on CPU tensors:
+    # inputs of the wrong size and output buffers that are too small are rejected; results are
+    # arrays over the caller's buffers, or views into one copy of the lane's buffers per batch
+    import torch
+    from paper_1512_02951_gb300 import api
+    from paper_1512_02951_gb300.serve import Request, _BatchCopy, _check_buffers, _result_in, _result_of
+    img = synth.make_image(16, 8, 1)
+    r = Request("protect", 16, 8, 5, 0, synth.make_iv(1), pixels=img)
+    _check_buffers(r)
+    with pytest.raises(ValueError):
+        _check_buffers(Request("protect", 16, 16, 5, 0, synth.make_iv(1), pixels=img))
+    n, pb, vb = r.sizes()
+    assert (n, pb, vb) == (16 * 8 * 3, 2 * 6 * 58, 2 * 6 * 6)
+    r.out = (torch.arange(pb + 4, dtype=torch.int64).to(torch.uint8), torch.zeros(vb - 1, dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        _check_buffers(r)
+    r.out = (r.out[0], torch.arange(vb, dtype=torch.uint8))
+    _check_buffers(r)
+    pub, priv = _result_in(r)
+    assert pub.shape == (1, 2, 3, 58) and pub.dtype == np.int16
+    assert pub.ctypes.data == r.out[0].data_ptr() and priv == bytes(range(vb))
+    rr = Request("restore", 16, 8, 5, 0, synth.make_iv(1), public=np.zeros(pb // 2, np.int16), private=bytes(vb))
+    _check_buffers(rr)
+    with pytest.raises(ValueError):
+        _check_buffers(Request("restore", 16, 8, 5, 0, synth.make_iv(1), public=np.zeros(pb, np.int16),
+                               private=bytes(vb)))
+    # builders: two restore requests in one batch, results as views into one copy
+    (offs, (npx, _, _)) = api.layout_arrays(np.array([n, n]), np.array([pb, pb]), np.array([vb, vb]))
+    lane_px = torch.from_numpy(np.random.default_rng(0).integers(0, 256, npx, dtype=np.uint8))
+    bc = _BatchCopy([lane_px, None], [npx, 0])
+    got = [_result_of(rr, (int(offs[0][i]), int(offs[1][i]), int(offs[2][i])), bc) for i in range(2)]
+    for i, g in enumerate(got):
+        assert g.shape == (8, 16, 3)
+        assert np.array_equal(g.reshape(-1), lane_px.numpy()[offs[0][i]: offs[0][i] + n])
+    before = [g.copy() for g in got]
+    lane_px.zero_()                       # the lane reuses its buffer: the results stay as they were
+    assert all(np.array_equal(g, b) for g, b in zip(got, before)) and before[0].any()
